@@ -1,0 +1,235 @@
+/*
+ * sdft.h -- C ABI of a single-GPU (GB300, sm_103a) real-space Kohn-Sham DFT solver:
+ * Chebyshev-filtered subspace iteration (CheFSI) inside the SCF loop, after the SPARC
+ * method (Xu et al., arXiv 2005.10431).
+ *
+ * Problem statement (paper Sec. 2, Eq. 1 and Eq. 2): for each spin s and k-point,
+ *     ( -1/2 Laplacian + V_eff^s[rho_up, rho_dn; R] ) psi_n = lambda_n psi_n,
+ *     rho^s(x) = sum_n g_n |psi_n(x)|^2,  g_n Fermi-Dirac,
+ * discretised on a uniform periodic grid with a 12th-order centred finite-difference
+ * Laplacian, a Gaussian-pseudocharge local pseudopotential with the Poisson problem for the
+ * electrostatic potential, and Kleinman-Bylander nonlocal projectors (paper Sec. 2.1).
+ *
+ * Conventions (all entry points):
+ *  - Atomic units (bohr, hartree).  Grid point (i,j,k) is at (i h1, j h2, k h3), h_d = L_d/n_d,
+ *    flat index g = i + n1 (j + n2 k).  dV = h1 h2 h3.
+ *  - Every function returns sdft_status: 0 on success, a negative SDFT_ERR_* code otherwise.
+ *    On error nothing is written to caller buffers unless stated; sdft_last_error() gives a
+ *    message (owned by the library, valid until the next call on that context/thread).
+ *  - Input arrays are owned by the caller and copied (host) or read (device) during the call.
+ *    Device buffers allocated by the library belong to the context and are released by
+ *    sdft_destroy().  The library never calls exit().
+ *  - "device" pointers are CUDA device addresses on the context's device; kernels run on the
+ *    stream given to sdft_create (NULL = legacy default stream).  Calls taking device output
+ *    pointers are asynchronous w.r.t. the host unless stated; calls writing host memory
+ *    synchronise the stream first.
+ *  - Orbital blocks on the device ("blocks") come in three storage kinds, selected by the
+ *    precision and the k-point:
+ *      SDFT_FP64, real (Gamma)   : double,  column-major ngrid x ncol  (column n at n*ngrid)
+ *      SDFT_FP64, complex (k!=0) : double2 (re,im), column-major ngrid x ncol
+ *      SDFT_MIXED, real (Gamma)  : float, "paired" layout: columns 2p and 2p+1 interleaved,
+ *                                  element (g, n) at ((n/2)*ngrid + g)*2 + (n%2); ncol even
+ *      SDFT_MIXED, complex       : float2 (re,im), column-major ngrid x ncol
+ *    Euclidean normalisation: the continuum orbital is X / sqrt(dV).
+ */
+#ifndef SDFT_H
+#define SDFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int sdft_status;
+
+#define SDFT_OK 0
+#define SDFT_ERR_INVALID_ARG (-1)   /* bad size, pointer, option, short output buffer */
+#define SDFT_ERR_OOM (-2)           /* allocation callback or cudaMalloc failed */
+#define SDFT_ERR_CUDA (-3)          /* a CUDA runtime / cuSOLVER call failed */
+#define SDFT_ERR_NOT_CONVERGED (-4) /* SCF or Poisson did not reach its tolerance */
+#define SDFT_ERR_CHOLESKY (-5)      /* subspace overlap matrix not positive definite */
+#define SDFT_ERR_DEVICE_TIMEOUT (-6)/* a bounded device-side wait gave up */
+#define SDFT_ERR_NONFINITE (-7)     /* NaN/Inf in an input or produced by the iteration */
+
+enum { SDFT_FP64 = 0, SDFT_MIXED = 1 };
+enum { SDFT_GUESS_SAD = 0, SDFT_GUESS_USER = 1 };
+
+typedef struct sdft_ctx sdft_ctx;
+
+/* Periodic orthorhombic cell (paper Sec. 2: Bloch-periodic BCs on orbitals, periodic on phi). */
+typedef struct {
+    double L[3];          /* edge lengths, bohr, > 0 */
+} sdft_cell;
+
+/* Uniform grid (paper Sec. 2.1).  fd_order must be 12 (radius 6). Each n[d] >= 6. */
+typedef struct {
+    int n[3];
+    int fd_order;
+} sdft_grid;
+
+/* Atoms: natom >= 1 positions (bohr, natom*3, x y z per atom) and species index per atom. */
+typedef struct {
+    int natom;
+    const double* pos;
+    const int* type;
+} sdft_atoms;
+
+/* Synthetic pseudo-atom (stands in for the paper's psp8 pseudopotentials, Sec. 2.2):
+ * pseudocharge b(r) = -Z (2 pi r_loc^2)^(-3/2) exp(-r^2/(2 r_loc^2)), r <= 10 r_loc;
+ * KB projector chi(r) = (pi^(3/2) r_proj^3)^(-1/2) exp(-r^2/(2 r_proj^2)), r < r_cut_proj,
+ * V_nl = sum_a E_kb |beta_a><beta_a|; SAD density Z (2 pi s^2)^(-3/2) exp(-r^2/(2 s^2)),
+ * r <= 10 s, s = sad_width. */
+typedef struct {
+    double Z, r_loc, r_proj, E_kb, r_cut_proj, sad_width;
+} sdft_pseudo;
+
+typedef struct {
+    int nspin;                 /* 1 (unpolarized, occupation factor 2) or 2 */
+    int nkpt;                  /* >= 1 */
+    const double* kpts;        /* nkpt*3 reduced coordinates (k.L/(2 pi)); NULL = Gamma */
+    const double* kw;          /* nkpt weights, sum 1; NULL = uniform */
+    int nstates;               /* orbitals per (spin, k) problem; even for SDFT_MIXED */
+    int cheb_degree;           /* Chebyshev filter degree m >= 1 */
+    int first_scf_filter_passes; /* CheFSI passes in the first SCF iteration (paper Sec. 2.1) */
+    int lanczos_steps;         /* Lanczos steps for the spectrum bounds */
+    double kT;                 /* Fermi-Dirac smearing, Ha */
+    int mix_hist;              /* Pulay history length (<= 16) */
+    double mix_beta;           /* mixing parameter */
+    int pulay_period;          /* Pulay extrapolation every pulay_period-th iteration */
+    int pulay_restart;         /* 1: clear the history after each Pulay step */
+    double scf_tol;            /* ||rho_out - rho_in|| / ||rho_out|| */
+    int max_scf;
+    int precision;             /* SDFT_FP64 or SDFT_MIXED */
+    int final_fp64_pass;       /* MIXED: one FP64 filter + Rayleigh-Ritz pass after the SCF */
+    double poisson_tol;        /* relative residual of the AAR Poisson solve */
+    int init_guess;            /* SDFT_GUESS_SAD or SDFT_GUESS_USER (see sdft_set_density) */
+    double initial_moment;     /* nspin=2: SAD split rho (1 +- m)/2 */
+    uint64_t seed;             /* counter-based generator seed for the initial orbitals */
+} sdft_options;
+
+/* Per-iteration record of the SCF (paper Sec. 2.1 ".out" progress). */
+typedef struct {
+    int iter;
+    double energy;     /* Harris-Foulkes free energy at rho_in, Ha */
+    double scf_error;  /* ||rho_out - rho_in|| / ||rho_out|| */
+    double mu;         /* Fermi level */
+    double seconds;    /* wall time since the start of sdft_scf (stream-synchronised) */
+    double lower, cutoff, upper; /* filter bounds a0, a, b of the first problem */
+} sdft_iter_record;
+
+typedef struct {
+    double energy;        /* free energy (Harris-Foulkes form), Ha */
+    double energy_ks;     /* Kohn-Sham form at the output density, Ha */
+    double mu;
+    double entropy_term;  /* -TS */
+    int niter;
+    int converged;
+    double t_total, t_filter, t_rr, t_poisson, t_other;  /* seconds */
+} sdft_result;
+
+typedef void* (*sdft_alloc_fn)(size_t bytes, void* user);
+typedef void (*sdft_free_fn)(void* ptr, void* user);
+
+/* Fill *opt with the defaults: nspin 1, Gamma, nstates 8, degree 12, 4 first-step passes,
+ * 20 Lanczos steps, kT 0.01, Pulay hist 7 / beta 0.3 / period 1 / no restart, scf_tol 1e-6,
+ * max_scf 100, FP64, no final pass, poisson_tol 1e-10, SAD, moment 0.125, seed 0. */
+void sdft_default_options(sdft_options* opt);
+
+/* Create a context: copies all inputs, builds the pseudocharge, projector tables and the SAD
+ * density on the device (paper Sec. 2.1 set-up).  alloc/free may be NULL (cudaMalloc/cudaFree).
+ * stream is a cudaStream_t (NULL = default stream).  Errors: INVALID_ARG (sizes, nonfinite
+ * positions -> NONFINITE), OOM, CUDA. */
+sdft_status sdft_create(const sdft_cell* cell, const sdft_grid* grid, const sdft_atoms* atoms,
+                        int ntypes, const sdft_pseudo* pseudo, const sdft_options* opt,
+                        sdft_alloc_fn alloc, sdft_free_fn free_fn, void* alloc_user,
+                        void* cuda_stream, sdft_ctx** out);
+void sdft_destroy(sdft_ctx* ctx);
+const char* sdft_last_error(const sdft_ctx* ctx);
+
+/* ---- full SCF (paper Sec. 2.1) ------------------------------------------------------ */
+
+/* Run the SCF from the current guess (SAD, or the density given by sdft_set_density) and the
+ * current orbitals (seeded, or given by sdft_set_orbitals).  Returns NOT_CONVERGED with the
+ * partial result filled in if max_scf is reached, CHOLESKY if the overlap matrix breaks down. */
+sdft_status sdft_scf(sdft_ctx* ctx, sdft_result* out);
+/* Re-seed the initial orbitals of every problem from opt.seed (as at create) and reset the
+ * density guess to the SAD (or last user) density, so that sdft_scf can be repeated. */
+sdft_status sdft_reset(sdft_ctx* ctx);
+
+/* Eigenvalues [spin][k][state], n >= nspin*nkpt*nstates. Host. */
+sdft_status sdft_get_eigenvalues(sdft_ctx* ctx, double* host, size_t n);
+/* Occupations g (same layout), host. */
+sdft_status sdft_get_occupations(sdft_ctx* ctx, double* host, size_t n);
+/* Output density of the last SCF iteration, [spin][ngrid]; dst on host or device. */
+sdft_status sdft_get_density(sdft_ctx* ctx, double* dst, size_t n, int on_device);
+/* Set the input density guess [spin][ngrid] (used when init_guess = SDFT_GUESS_USER). */
+sdft_status sdft_set_density(sdft_ctx* ctx, const double* src, size_t n, int on_device);
+/* Hellmann-Feynman forces after sdft_scf, natom*3, Ha/bohr, host. */
+sdft_status sdft_get_forces(sdft_ctx* ctx, double* host, size_t n);
+/* Per-iteration records of the last sdft_scf; *count receives the number available. */
+sdft_status sdft_get_scf_log(sdft_ctx* ctx, sdft_iter_record* host, size_t cap, size_t* count);
+/* Pseudocharge b [ngrid] and SAD density [ngrid] as built at create (host or device). */
+sdft_status sdft_get_pseudocharge(sdft_ctx* ctx, double* dst, size_t n, int on_device);
+sdft_status sdft_get_sad_density(sdft_ctx* ctx, double* dst, size_t n, int on_device);
+/* Orbitals of problem (spin, k) in the storage kind of `precision` (see header notes):
+ * copy from/to a caller device buffer of the block's size. */
+sdft_status sdft_set_orbitals(sdft_ctx* ctx, int spin, int kpt, const void* dev, size_t bytes);
+sdft_status sdft_get_orbitals(sdft_ctx* ctx, int spin, int kpt, void* dev, size_t bytes);
+
+/* ---- hot-path steps, exposed one by one (paper Sec. 2.1 CheFSI) ---------------------- */
+
+/* Set V_eff^spin [ngrid] (FP64, host or device); the FP32 copy used by SDFT_MIXED is updated. */
+sdft_status sdft_set_veff(sdft_ctx* ctx, int spin, const double* v, int on_device);
+
+/* Y = H X for ncol columns of problem (spin, kpt) in `precision` (device blocks; paper Eq. 1,
+ * matrix-free: 12th-order FD stencil + V_eff + KB projectors). */
+sdft_status sdft_apply_h(sdft_ctx* ctx, int spin, int kpt, int precision,
+                         const void* x, void* y, int ncol);
+
+/* Degree-m scaled Chebyshev filter (Zhou-Saad): Y = p_m(H) X with the interval [a, b] mapped
+ * to [-1, 1] and p_m(a0) = 1.  x is not modified; y receives the result (device blocks). */
+sdft_status sdft_chebyshev_filter(sdft_ctx* ctx, int spin, int kpt, int precision,
+                                  const void* x, void* y, int ncol, int degree,
+                                  double a, double b, double a0);
+
+/* Rayleigh-Ritz on the block y (device): M = Y^H Y, Hs = Y^H H Y, Hs q = lambda M q,
+ * x = Y Q.  eig receives ncol eigenvalues ascending (device, FP64). */
+sdft_status sdft_rayleigh_ritz(sdft_ctx* ctx, int spin, int kpt, int precision,
+                               const void* y, void* x, double* eig, int ncol);
+
+/* Subspace matrices only: M = Y^H Y and Hs = Y^H (H Y) as FP64 ncol x ncol (device,
+ * column-major; complex problems write double2).  hy is the device block H Y. */
+sdft_status sdft_subspace_matrices(sdft_ctx* ctx, int kpt, int precision, const void* y,
+                                   const void* hy, void* m, void* hs, int ncol);
+
+/* Rotation x = y Q for an FP64 ncol x ncol column-major Q (double2 for complex), device. */
+sdft_status sdft_rotate(sdft_ctx* ctx, int kpt, int precision, const void* y, const void* q,
+                        void* x, int ncol);
+
+/* Poisson: -L phi = 4 pi (f - mean f), zero-mean phi, by AAR (paper Sec. 2.1; Pratapa,
+ * Suryanarayana & Pask 2016).  f, phi: device FP64 [ngrid]; phi is also the initial guess.
+ * *iters receives the iteration count.  NOT_CONVERGED if the tolerance is not reached. */
+sdft_status sdft_poisson(sdft_ctx* ctx, const double* f, double* phi, double tol, int max_iter,
+                         int* iters);
+
+/* Perdew-Zunger LDA (paper Sec. 3): rho [nspin][n] -> eps_xc [n], v_xc [nspin][n]; device FP64. */
+sdft_status sdft_lda(sdft_ctx* ctx, int nspin, const double* rho, double* exc, double* vxc,
+                     size_t n);
+
+/* Fermi level by bisection on sum_k w_k sum_n g = N_e; eig [nspin][nkpt][nstates] (device);
+ * occ receives g (device), mu/ts written to host scalars. */
+sdft_status sdft_fermi(sdft_ctx* ctx, const double* eig, double* occ, double* mu, double* ts);
+
+/* Spectrum bounds by Lanczos on problem (spin, kpt): lower Ritz value, upper bound. Host out. */
+sdft_status sdft_lanczos_bounds(sdft_ctx* ctx, int spin, int kpt, int steps, double* lower,
+                                double* upper);
+
+/* Number of kernel launches the library has issued on this context (for benchmarks). */
+sdft_status sdft_launch_count(const sdft_ctx* ctx, uint64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDFT_H */

@@ -1,0 +1,538 @@
+// extern "C" entry points of libsdft (declared in include/sdft.h).  Every entry point
+// converts internal exceptions into an sdft_status and keeps the message for sdft_last_error.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace sdft {
+
+void* ctx_alloc(sdft_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (c->alloc) {
+        p = c->alloc(bytes, c->alloc_user);
+        SDFT_REQUIRE(p != nullptr, SDFT_ERR_OOM, "allocation callback returned NULL for " + std::to_string(bytes) + " bytes");
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{SDFT_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+        }
+    }
+    c->owned.push_back(p);
+    SDFT_CUDA(cudaMemsetAsync(p, 0, bytes, c->stream));
+    return p;
+}
+
+void ctx_free_all(sdft_ctx* c) {
+    if (c->stream || true) cudaStreamSynchronize(c->stream);
+    for (void* p : c->owned) {
+        if (c->release) c->release(p, c->alloc_user);
+        else cudaFree(p);
+    }
+    c->owned.clear();
+    if (c->hscal) {
+        cudaFreeHost(c->hscal);
+        c->hscal = nullptr;
+    }
+}
+
+namespace {
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+void host_energy_constants(sdft_ctx* c) {
+    // E_self = sum Z^2 / (2 sqrt(pi) r_loc); E_sc = 1/2 sum' Z Z' erfc(d/s)/d, s = sqrt(2(r^2 + r'^2))
+    c->E_self = 0.0;
+    for (int a = 0; a < c->natom; ++a) {
+        const sdft_pseudo& s = c->species[c->types[a]];
+        c->E_self += s.Z * s.Z / (2.0 * std::sqrt(M_PI) * s.r_loc);
+    }
+    c->E_sc = 0.0;
+    c->dEsc.assign(3 * c->natom, 0.0);
+    const double rmax = 30.0;
+    int nimg[3];
+    for (int d = 0; d < 3; ++d) nimg[d] = (int)std::ceil(rmax / c->L[d]) + 1;
+    for (int a = 0; a < c->natom; ++a) {
+        const sdft_pseudo& sa = c->species[c->types[a]];
+        for (int b = 0; b < c->natom; ++b) {
+            const sdft_pseudo& sb = c->species[c->types[b]];
+            const double s = std::sqrt(2.0 * (sa.r_loc * sa.r_loc + sb.r_loc * sb.r_loc));
+            for (int t0 = -nimg[0]; t0 <= nimg[0]; ++t0)
+                for (int t1 = -nimg[1]; t1 <= nimg[1]; ++t1)
+                    for (int t2 = -nimg[2]; t2 <= nimg[2]; ++t2) {
+                        if (a == b && t0 == 0 && t1 == 0 && t2 == 0) continue;
+                        const double v[3] = {c->pos[3 * a] - c->pos[3 * b] - t0 * c->L[0],
+                                             c->pos[3 * a + 1] - c->pos[3 * b + 1] - t1 * c->L[1],
+                                             c->pos[3 * a + 2] - c->pos[3 * b + 2] - t2 * c->L[2]};
+                        const double d = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                        if (d > rmax) continue;
+                        c->E_sc += 0.5 * sa.Z * sb.Z * std::erfc(d / s) / d;
+                        if (a != b) {
+                            const double f = sa.Z * sb.Z *
+                                             (-2.0 / (s * std::sqrt(M_PI)) * std::exp(-(d / s) * (d / s)) / d -
+                                              std::erfc(d / s) / (d * d));
+                            for (int q = 0; q < 3; ++q) c->dEsc[3 * a + q] += f * v[q] / d;
+                        }
+                    }
+        }
+    }
+}
+
+void build_context(sdft_ctx* c) {
+    const sdft_options& o = c->opt;
+    const long long ng = c->ng;
+    const int ns = o.nstates;
+    SDFT_CUDA(cudaMallocHost(&c->hscal, sizeof(double) * SCAL_DOUBLES));
+    cusolverStatus_t cs = cusolverDnCreate(&c->solver);
+    SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "cusolverDnCreate failed");
+    cusolverDnSetStream(c->solver, c->stream);
+    c->scal = (double*)ctx_alloc(c, sizeof(double) * SCAL_DOUBLES);
+    c->b = (double*)ctx_alloc(c, sizeof(double) * ng);
+    c->rho_sad = (double*)ctx_alloc(c, sizeof(double) * ng);
+    c->rho_user = (double*)ctx_alloc(c, sizeof(double) * o.nspin * ng);
+    c->rho_in = (double*)ctx_alloc(c, sizeof(double) * o.nspin * ng);
+    c->rho_out = (double*)ctx_alloc(c, sizeof(double) * o.nspin * ng);
+    c->phi = (double*)ctx_alloc(c, sizeof(double) * ng);
+    c->veff = (double*)ctx_alloc(c, sizeof(double) * o.nspin * ng);
+    c->veff32 = (float*)ctx_alloc(c, sizeof(float) * o.nspin * ng);
+    c->exc = (double*)ctx_alloc(c, sizeof(double) * ng);
+    c->work64 = (double*)ctx_alloc(c, sizeof(double) * 28 * ng);
+    // FD coefficients of -1/2 L_h
+    const double w[7] = {-5369.0 / 1800.0, 12.0 / 7.0, -15.0 / 56.0, 10.0 / 189.0, -1.0 / 112.0, 2.0 / 1925.0,
+                         -1.0 / 16632.0};
+    double c0 = 0.0;
+    for (int r = 0; r <= FD_RADIUS; ++r) {
+        c->coef.cx[r] = -0.5 * w[r] / (c->h[0] * c->h[0]);
+        c->coef.cy[r] = -0.5 * w[r] / (c->h[1] * c->h[1]);
+        c->coef.cz[r] = -0.5 * w[r] / (c->h[2] * c->h[2]);
+    }
+    c0 = c->coef.cx[0] + c->coef.cy[0] + c->coef.cz[0];
+    c->coef.c0 = c0;
+    // geometry set-up on the device
+    build_pseudocharge_and_sad(c);
+    c->kb.resize(o.nkpt);
+    bool any_cplx = false;
+    for (int k = 0; k < o.nkpt; ++k) {
+        build_kb_tables(c, k);
+        any_cplx = any_cplx || c->kb[k].cplx;
+    }
+    host_energy_constants(c);
+    // problems
+    const int np = o.nspin * o.nkpt;
+    double* eig_all = (double*)ctx_alloc(c, sizeof(double) * np * ns);
+    double* occ_all = (double*)ctx_alloc(c, sizeof(double) * np * ns);
+    c->probs.resize(np);
+    size_t maxblock = 0;
+    for (int s = 0; s < o.nspin; ++s)
+        for (int k = 0; k < o.nkpt; ++k) {
+            Problem& P = c->probs[s * o.nkpt + k];
+            P.spin = s;
+            P.kpt = k;
+            P.cplx = c->kb[k].cplx;
+            const size_t bytes = block_elems_bytes(c, o.precision, P.cplx, ns);
+            P.X = ctx_alloc(c, bytes);
+            if (o.precision == SDFT_MIXED) P.X64 = ctx_alloc(c, block_elems_bytes(c, SDFT_FP64, P.cplx, ns));
+            P.eig = eig_all + (long long)(s * o.nkpt + k) * ns;
+            P.occ = occ_all + (long long)(s * o.nkpt + k) * ns;
+            maxblock = std::max(maxblock, bytes);
+            if (o.precision == SDFT_MIXED) maxblock = std::max(maxblock, block_elems_bytes(c, SDFT_FP64, P.cplx, ns));
+        }
+    c->block_bytes = maxblock;
+    for (int i = 0; i < 4; ++i) c->blk[i] = ctx_alloc(c, maxblock);
+    const int w2 = any_cplx ? 2 : 1;
+    c->Ms = (double*)ctx_alloc(c, sizeof(double) * ns * ns * w2);
+    c->Hs = (double*)ctx_alloc(c, sizeof(double) * ns * ns * w2);
+    c->part_elems = std::max<size_t>((size_t)2 * ns * ns * w2 * 64, 1 << 20);
+    c->part = (double*)ctx_alloc(c, sizeof(double) * c->part_elems);
+    c->dscale = (double*)ctx_alloc(c, sizeof(double) * ns);
+    c->Q32 = ctx_alloc(c, sizeof(float) * ns * ns * w2);
+    c->C32 = (float*)ctx_alloc(c, sizeof(float) * 2 * std::max(1, c->natom) * ns);
+    c->C64 = (double*)ctx_alloc(c, sizeof(double) * 2 * std::max(1, c->natom) * ns);
+    c->dinfo = (int*)ctx_alloc(c, sizeof(int) * 4);
+    // cuSOLVER workspace for the generalized eigenproblem of size ns
+    int lw = 0;
+    if (any_cplx) {
+        cs = cusolverDnZhegvd_bufferSize(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                         CUBLAS_FILL_MODE_UPPER, ns, (cuDoubleComplex*)c->Hs, ns,
+                                         (cuDoubleComplex*)c->Ms, ns, c->dscale, &lw);
+        SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "hegvd workspace query failed");
+        c->solver_lwork = lw;
+    }
+    cs = cusolverDnDsygvd_bufferSize(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER,
+                                     ns, c->Hs, ns, c->Ms, ns, c->dscale, &lw);
+    SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "sygvd workspace query failed");
+    c->solver_lwork = std::max(c->solver_lwork, lw);
+    c->solver_work = ctx_alloc(c, (size_t)c->solver_lwork * 16 + 256);
+    // mixing history
+    const long long nv = (long long)o.nspin * ng;
+    c->mix_dx = (double*)ctx_alloc(c, sizeof(double) * nv * o.mix_hist);
+    c->mix_df = (double*)ctx_alloc(c, sizeof(double) * nv * o.mix_hist);
+    c->mix_xprev = (double*)ctx_alloc(c, sizeof(double) * nv);
+    c->mix_fprev = (double*)ctx_alloc(c, sizeof(double) * nv);
+    reset_state(c);
+    SDFT_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+sdft_status fail(sdft_ctx* c, const Error& e) {
+    if (c) c->last_error = e.msg;
+    return e.code;
+}
+
+thread_local std::string g_create_error;
+
+}  // namespace
+}  // namespace sdft
+
+using sdft::Error;
+
+#define SDFT_TRY(ctx, ...)                                                     \
+    try {                                                                      \
+        if (!(ctx)) return SDFT_ERR_INVALID_ARG;                               \
+        (ctx)->last_error.clear();                                             \
+        __VA_ARGS__;                                                               \
+        return SDFT_OK;                                                        \
+    } catch (const Error& e) {                                                 \
+        return sdft::fail((ctx), e);                                           \
+    } catch (const std::exception& e) {                                        \
+        (ctx)->last_error = e.what();                                          \
+        return SDFT_ERR_CUDA;                                                  \
+    }
+
+extern "C" {
+
+void sdft_default_options(sdft_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->nspin = 1;
+    o->nkpt = 1;
+    o->nstates = 8;
+    o->cheb_degree = 12;
+    o->first_scf_filter_passes = 4;
+    o->lanczos_steps = 20;
+    o->kT = 0.01;
+    o->mix_hist = 7;
+    o->mix_beta = 0.3;
+    o->pulay_period = 1;
+    o->pulay_restart = 0;
+    o->scf_tol = 1e-6;
+    o->max_scf = 100;
+    o->precision = SDFT_FP64;
+    o->final_fp64_pass = 0;
+    o->poisson_tol = 1e-10;
+    o->init_guess = SDFT_GUESS_SAD;
+    o->initial_moment = 0.125;
+    o->seed = 0;
+}
+
+sdft_status sdft_create(const sdft_cell* cell, const sdft_grid* grid, const sdft_atoms* atoms, int ntypes,
+                        const sdft_pseudo* pseudo, const sdft_options* opt, sdft_alloc_fn alloc, sdft_free_fn free_fn,
+                        void* alloc_user, void* cuda_stream, sdft_ctx** out) {
+    if (!out) return SDFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    sdft_ctx* c = new sdft_ctx();
+    try {
+        SDFT_REQUIRE(cell && grid && atoms && pseudo && opt, SDFT_ERR_INVALID_ARG, "null argument");
+        SDFT_REQUIRE(grid->fd_order == 12, SDFT_ERR_INVALID_ARG, "fd_order must be 12");
+        SDFT_REQUIRE(ntypes >= 1, SDFT_ERR_INVALID_ARG, "ntypes must be >= 1");
+        SDFT_REQUIRE(atoms->natom >= 1 && atoms->pos && atoms->type, SDFT_ERR_INVALID_ARG, "atoms");
+        SDFT_REQUIRE(sdft::finite_all(atoms->pos, 3 * (size_t)atoms->natom), SDFT_ERR_NONFINITE,
+                     "atom positions contain NaN/Inf");
+        SDFT_REQUIRE(sdft::finite_all(cell->L, 3), SDFT_ERR_NONFINITE, "cell contains NaN/Inf");
+        for (int d = 0; d < 3; ++d) {
+            SDFT_REQUIRE(cell->L[d] > 0, SDFT_ERR_INVALID_ARG, "cell edges must be positive");
+            SDFT_REQUIRE(grid->n[d] >= 6, SDFT_ERR_INVALID_ARG, "grid points per edge must be >= 6");
+        }
+        for (int t = 0; t < ntypes; ++t) {
+            const sdft_pseudo& p = pseudo[t];
+            const double v[6] = {p.Z, p.r_loc, p.r_proj, p.E_kb, p.r_cut_proj, p.sad_width};
+            SDFT_REQUIRE(sdft::finite_all(v, 6), SDFT_ERR_NONFINITE, "pseudopotential contains NaN/Inf");
+            SDFT_REQUIRE(p.Z > 0 && p.r_loc > 0 && p.r_proj > 0 && p.r_cut_proj > 0 && p.sad_width > 0,
+                         SDFT_ERR_INVALID_ARG, "pseudopotential parameters must be positive");
+        }
+        for (int a = 0; a < atoms->natom; ++a)
+            SDFT_REQUIRE(atoms->type[a] >= 0 && atoms->type[a] < ntypes, SDFT_ERR_INVALID_ARG, "atom type out of range");
+        const sdft_options& o = *opt;
+        SDFT_REQUIRE(o.nspin == 1 || o.nspin == 2, SDFT_ERR_INVALID_ARG, "nspin must be 1 or 2");
+        SDFT_REQUIRE(o.nkpt >= 1 && o.nkpt <= sdft::MAX_KPT, SDFT_ERR_INVALID_ARG, "nkpt must be in [1, 256]");
+        SDFT_REQUIRE(o.nstates >= 2, SDFT_ERR_INVALID_ARG, "nstates must be >= 2");
+        SDFT_REQUIRE(o.precision == SDFT_FP64 || o.precision == SDFT_MIXED, SDFT_ERR_INVALID_ARG, "precision");
+        SDFT_REQUIRE(o.precision == SDFT_FP64 || o.nstates % 2 == 0, SDFT_ERR_INVALID_ARG,
+                     "SDFT_MIXED needs an even number of states");
+        SDFT_REQUIRE(o.cheb_degree >= 1 && o.lanczos_steps >= 2, SDFT_ERR_INVALID_ARG, "degree / lanczos steps");
+        SDFT_REQUIRE(o.kT > 0 && std::isfinite(o.kT), SDFT_ERR_INVALID_ARG, "kT must be positive");
+        SDFT_REQUIRE(o.mix_hist >= 1 && o.mix_hist <= 16, SDFT_ERR_INVALID_ARG, "mix_hist must be in [1, 16]");
+        SDFT_REQUIRE(o.pulay_period >= 1, SDFT_ERR_INVALID_ARG, "pulay_period must be >= 1");
+        SDFT_REQUIRE(o.max_scf >= 1, SDFT_ERR_INVALID_ARG, "max_scf must be >= 1");
+        c->opt = o;
+        c->stream = (cudaStream_t)cuda_stream;
+        c->alloc = alloc;
+        c->release = free_fn;
+        c->alloc_user = alloc_user;
+        for (int d = 0; d < 3; ++d) {
+            c->n[d] = grid->n[d];
+            c->L[d] = cell->L[d];
+            c->h[d] = cell->L[d] / grid->n[d];
+        }
+        c->dV = c->h[0] * c->h[1] * c->h[2];
+        c->ng = (long long)c->n[0] * c->n[1] * c->n[2];
+        c->natom = atoms->natom;
+        c->pos.assign(atoms->pos, atoms->pos + 3 * atoms->natom);
+        c->types.assign(atoms->type, atoms->type + atoms->natom);
+        c->species.assign(pseudo, pseudo + ntypes);
+        c->nelec = 0.0;
+        for (int a = 0; a < c->natom; ++a) c->nelec += c->species[c->types[a]].Z;
+        c->kpts.assign(3 * o.nkpt, 0.0);
+        if (o.kpts) {
+            SDFT_REQUIRE(sdft::finite_all(o.kpts, 3 * (size_t)o.nkpt), SDFT_ERR_NONFINITE, "k-points contain NaN/Inf");
+            c->kpts.assign(o.kpts, o.kpts + 3 * o.nkpt);
+        }
+        c->kw.assign(o.nkpt, 1.0 / o.nkpt);
+        if (o.kw) c->kw.assign(o.kw, o.kw + o.nkpt);
+        c->opt.kpts = nullptr;
+        c->opt.kw = nullptr;
+        const double nfill = c->nelec / (o.nspin == 1 ? 2.0 : 1.0) / (o.nspin == 1 ? 1.0 : 2.0);
+        SDFT_REQUIRE(o.nstates >= (int)std::ceil(nfill), SDFT_ERR_INVALID_ARG, "nstates below the occupied count");
+        sdft::build_context(c);
+        *out = c;
+        return SDFT_OK;
+    } catch (const Error& e) {
+        sdft::g_create_error = e.msg;
+        sdft::ctx_free_all(c);
+        if (c->solver) cusolverDnDestroy(c->solver);
+        delete c;
+        return e.code;
+    }
+}
+
+void sdft_destroy(sdft_ctx* c) {
+    if (!c) return;
+    sdft::ctx_free_all(c);
+    if (c->solver) cusolverDnDestroy(c->solver);
+    delete c;
+}
+
+const char* sdft_last_error(const sdft_ctx* c) {
+    if (!c) return sdft::g_create_error.c_str();
+    return c->last_error.c_str();
+}
+
+sdft_status sdft_scf(sdft_ctx* c, sdft_result* out) {
+    try {
+        if (!c) return SDFT_ERR_INVALID_ARG;
+        c->last_error.clear();
+        const sdft_status s = sdft::run_scf(c, out);
+        if (s == SDFT_ERR_NOT_CONVERGED) c->last_error = "SCF did not reach scf_tol within max_scf iterations";
+        return s;
+    } catch (const Error& e) {
+        return sdft::fail(c, e);
+    }
+}
+
+sdft_status sdft_reset(sdft_ctx* c) { SDFT_TRY(c, { sdft::reset_state(c); SDFT_CUDA(cudaStreamSynchronize(c->stream)); }) }
+
+static sdft_status copy_out(sdft_ctx* c, const std::vector<double>& v, double* host, size_t n) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(host != nullptr, SDFT_ERR_INVALID_ARG, "null output");
+        SDFT_REQUIRE(!v.empty(), SDFT_ERR_INVALID_ARG, "no result available (run sdft_scf first)");
+        SDFT_REQUIRE(n >= v.size(), SDFT_ERR_INVALID_ARG, "output buffer too short");
+        std::memcpy(host, v.data(), sizeof(double) * v.size());
+    })
+}
+
+sdft_status sdft_get_eigenvalues(sdft_ctx* c, double* host, size_t n) { return copy_out(c, c ? c->eig_host : std::vector<double>(), host, n); }
+sdft_status sdft_get_occupations(sdft_ctx* c, double* host, size_t n) { return copy_out(c, c ? c->occ_host : std::vector<double>(), host, n); }
+sdft_status sdft_get_forces(sdft_ctx* c, double* host, size_t n) { return copy_out(c, c ? c->forces : std::vector<double>(), host, n); }
+
+static sdft_status copy_field(sdft_ctx* c, const double* src, size_t count, double* dst, size_t n, int on_device) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(dst != nullptr, SDFT_ERR_INVALID_ARG, "null output");
+        SDFT_REQUIRE(n >= count, SDFT_ERR_INVALID_ARG, "output buffer too short");
+        SDFT_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * count,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_get_density(sdft_ctx* c, double* dst, size_t n, int on_device) {
+    if (!c) return SDFT_ERR_INVALID_ARG;
+    return copy_field(c, c->rho_out, (size_t)c->opt.nspin * c->ng, dst, n, on_device);
+}
+sdft_status sdft_get_pseudocharge(sdft_ctx* c, double* dst, size_t n, int on_device) {
+    if (!c) return SDFT_ERR_INVALID_ARG;
+    return copy_field(c, c->b, (size_t)c->ng, dst, n, on_device);
+}
+sdft_status sdft_get_sad_density(sdft_ctx* c, double* dst, size_t n, int on_device) {
+    if (!c) return SDFT_ERR_INVALID_ARG;
+    return copy_field(c, c->rho_sad, (size_t)c->ng, dst, n, on_device);
+}
+
+sdft_status sdft_set_density(sdft_ctx* c, const double* src, size_t n, int on_device) {
+    SDFT_TRY(c, {
+        const size_t need = (size_t)c->opt.nspin * c->ng;
+        SDFT_REQUIRE(src != nullptr && n == need, SDFT_ERR_INVALID_ARG, "density size must be nspin*ngrid");
+        if (!on_device) SDFT_REQUIRE(sdft::finite_all(src, n), SDFT_ERR_NONFINITE, "density contains NaN/Inf");
+        SDFT_CUDA(cudaMemcpyAsync(c->rho_user, src, sizeof(double) * n,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+        SDFT_CUDA(cudaMemcpyAsync(c->rho_in, c->rho_user, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        c->user_density = true;
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_get_scf_log(sdft_ctx* c, sdft_iter_record* host, size_t cap, size_t* count) {
+    SDFT_TRY(c, {
+        if (count) *count = c->log.size();
+        if (host) std::memcpy(host, c->log.data(), sizeof(sdft_iter_record) * std::min(cap, c->log.size()));
+    })
+}
+
+static sdft::Problem& problem_of(sdft_ctx* c, int spin, int kpt) {
+    SDFT_REQUIRE(spin >= 0 && spin < c->opt.nspin && kpt >= 0 && kpt < c->opt.nkpt, SDFT_ERR_INVALID_ARG,
+                 "spin / k-point index out of range");
+    return c->probs[spin * c->opt.nkpt + kpt];
+}
+
+sdft_status sdft_set_orbitals(sdft_ctx* c, int spin, int kpt, const void* dev, size_t bytes) {
+    SDFT_TRY(c, {
+        sdft::Problem& P = problem_of(c, spin, kpt);
+        const size_t need = sdft::block_elems_bytes(c, c->opt.precision, P.cplx, c->opt.nstates);
+        SDFT_REQUIRE(dev != nullptr && bytes == need, SDFT_ERR_INVALID_ARG, "orbital block size mismatch");
+        SDFT_CUDA(cudaMemcpyAsync(P.X, dev, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_get_orbitals(sdft_ctx* c, int spin, int kpt, void* dev, size_t bytes) {
+    SDFT_TRY(c, {
+        sdft::Problem& P = problem_of(c, spin, kpt);
+        const size_t need = sdft::block_elems_bytes(c, c->opt.precision, P.cplx, c->opt.nstates);
+        SDFT_REQUIRE(dev != nullptr && bytes == need, SDFT_ERR_INVALID_ARG, "orbital block size mismatch");
+        SDFT_CUDA(cudaMemcpyAsync(dev, P.X, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_set_veff(sdft_ctx* c, int spin, const double* v, int on_device) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(spin >= 0 && spin < c->opt.nspin && v, SDFT_ERR_INVALID_ARG, "spin / pointer");
+        if (!on_device) SDFT_REQUIRE(sdft::finite_all(v, (size_t)c->ng), SDFT_ERR_NONFINITE, "V_eff contains NaN/Inf");
+        double* dst = c->veff + (long long)spin * c->ng;
+        SDFT_CUDA(cudaMemcpyAsync(dst, v, sizeof(double) * c->ng,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+        sdft::veff_to_float(c, spin);
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+static void check_block_args(sdft_ctx* c, int spin, int kpt, int precision, int ncol) {
+    SDFT_REQUIRE(spin >= 0 && spin < c->opt.nspin && kpt >= 0 && kpt < c->opt.nkpt, SDFT_ERR_INVALID_ARG,
+                 "spin / k-point index out of range");
+    SDFT_REQUIRE(precision == SDFT_FP64 || precision == SDFT_MIXED, SDFT_ERR_INVALID_ARG, "precision");
+    SDFT_REQUIRE(ncol >= 1 && ncol <= c->opt.nstates, SDFT_ERR_INVALID_ARG, "ncol must be in [1, nstates]");
+    SDFT_REQUIRE(precision == SDFT_FP64 || c->kb[kpt].cplx || ncol % 2 == 0, SDFT_ERR_INVALID_ARG,
+                 "SDFT_MIXED real blocks need an even column count");
+}
+
+sdft_status sdft_apply_h(sdft_ctx* c, int spin, int kpt, int precision, const void* x, void* y, int ncol) {
+    SDFT_TRY(c, {
+        check_block_args(c, spin, kpt, precision, ncol);
+        SDFT_REQUIRE(x && y && x != y, SDFT_ERR_INVALID_ARG, "x, y must be distinct device blocks");
+        sdft::apply_h(c, kpt, precision, x, y, ncol, c->veff + (long long)spin * c->ng,
+                      c->veff32 + (long long)spin * c->ng);
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_chebyshev_filter(sdft_ctx* c, int spin, int kpt, int precision, const void* x, void* y, int ncol,
+                                  int degree, double a, double b, double a0) {
+    SDFT_TRY(c, {
+        check_block_args(c, spin, kpt, precision, ncol);
+        SDFT_REQUIRE(x && y && x != y, SDFT_ERR_INVALID_ARG, "x, y must be distinct device blocks");
+        sdft::chebyshev_filter(c, kpt, precision, x, y, ncol, degree, a, b, a0, c->veff + (long long)spin * c->ng,
+                               c->veff32 + (long long)spin * c->ng);
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_rayleigh_ritz(sdft_ctx* c, int spin, int kpt, int precision, const void* y, void* x, double* eig,
+                               int ncol) {
+    SDFT_TRY(c, {
+        check_block_args(c, spin, kpt, precision, ncol);
+        SDFT_REQUIRE(x && y && eig && x != y, SDFT_ERR_INVALID_ARG, "pointers");
+        sdft::rayleigh_ritz(c, kpt, precision, y, x, eig, ncol, c->veff + (long long)spin * c->ng,
+                            c->veff32 + (long long)spin * c->ng);
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_subspace_matrices(sdft_ctx* c, int kpt, int precision, const void* y, const void* hy, void* m,
+                                   void* hs, int ncol) {
+    SDFT_TRY(c, {
+        check_block_args(c, 0, kpt, precision, ncol);
+        SDFT_REQUIRE(y && hy && m && hs, SDFT_ERR_INVALID_ARG, "pointers");
+        sdft::subspace_gram(c, precision, c->kb[kpt].cplx, y, hy, (double*)m, (double*)hs, ncol);
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_rotate(sdft_ctx* c, int kpt, int precision, const void* y, const void* q, void* x, int ncol) {
+    SDFT_TRY(c, {
+        check_block_args(c, 0, kpt, precision, ncol);
+        SDFT_REQUIRE(y && q && x && x != y, SDFT_ERR_INVALID_ARG, "pointers");
+        sdft::rotate_block(c, precision, c->kb[kpt].cplx, y, (const double*)q, x, ncol);
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_poisson(sdft_ctx* c, const double* f, double* phi, double tol, int max_iter, int* iters) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(f && phi && tol > 0 && max_iter >= 1, SDFT_ERR_INVALID_ARG, "arguments");
+        const int it = sdft::poisson_aar(c, f, phi, tol, max_iter);
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+        if (iters) *iters = it < 0 ? -it : it;
+        if (it < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Poisson AAR did not reach the tolerance"};
+    })
+}
+
+sdft_status sdft_lda(sdft_ctx* c, int nspin, const double* rho, double* exc, double* vxc, size_t n) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE((nspin == 1 || nspin == 2) && rho && exc && vxc, SDFT_ERR_INVALID_ARG, "arguments");
+        sdft::lda_device(c, nspin, rho, exc, vxc, n);
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_fermi(sdft_ctx* c, const double* eig, double* occ, double* mu, double* ts) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(eig && occ, SDFT_ERR_INVALID_ARG, "pointers");
+        sdft::fermi_device(c, eig, occ, c->scal + 8);
+        double h[3];
+        SDFT_CUDA(cudaMemcpyAsync(h, c->scal + 8, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+        if (mu) *mu = h[0];
+        if (ts) *ts = h[1];
+    })
+}
+
+sdft_status sdft_lanczos_bounds(sdft_ctx* c, int spin, int kpt, int steps, double* lower, double* upper) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(spin >= 0 && spin < c->opt.nspin && kpt >= 0 && kpt < c->opt.nkpt && steps >= 2 && lower && upper,
+                     SDFT_ERR_INVALID_ARG, "arguments");
+        sdft::lanczos(c, spin, kpt, steps, lower, upper);
+    })
+}
+
+sdft_status sdft_launch_count(const sdft_ctx* c, uint64_t* count) {
+    if (!c || !count) return SDFT_ERR_INVALID_ARG;
+    *count = c->launches;
+    return SDFT_OK;
+}
+
+}  // extern "C"

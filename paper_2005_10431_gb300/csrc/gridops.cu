@@ -1,0 +1,843 @@
+// Grid-level FP64 kernels of the SCF (paper Sec. 2.1): pseudocharges and the SAD guess,
+// Perdew-Zunger LDA, the AAR Poisson solver, density from orbitals (Eq. 2), Fermi-Dirac
+// occupations, Pulay mixing, reductions and Hellmann-Feynman forces.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace sdft {
+namespace {
+
+constexpr int RB = 256;   // reduction block size
+constexpr int RGRID = 512; // reduction blocks
+
+// ---------------------------------------------------------------------------------------
+// set-up: pseudocharge b and SAD density, summed over periodic images within the cutoff
+// ---------------------------------------------------------------------------------------
+struct AtomG {
+    double pos[3];
+    double amp_b, w_b, cut_b;      // pseudocharge amplitude, width, cutoff
+    double amp_s, w_s, cut_s;      // SAD
+};
+
+__device__ double image_sum(double x, double y, double z, const double* pos, double L1, double L2, double L3,
+                            double amp, double w, double cut) {
+    double s = 0.0;
+    const double L[3] = {L1, L2, L3};
+    const double X[3] = {x, y, z};
+    int tlo[3], thi[3];
+    for (int d = 0; d < 3; ++d) {
+        tlo[d] = (int)ceil((X[d] - pos[d] - cut) / L[d]);
+        thi[d] = (int)floor((X[d] - pos[d] + cut) / L[d]);
+    }
+    const double inv = 1.0 / (2.0 * w * w);
+    for (int t2 = tlo[2]; t2 <= thi[2]; ++t2)
+        for (int t1 = tlo[1]; t1 <= thi[1]; ++t1)
+            for (int t0 = tlo[0]; t0 <= thi[0]; ++t0) {
+                const double dx = X[0] - pos[0] - t0 * L1, dy = X[1] - pos[1] - t1 * L2, dz = X[2] - pos[2] - t2 * L3;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 <= cut * cut) s += amp * exp(-r2 * inv);
+            }
+    return s;
+}
+
+__global__ void setup_fields_kernel(const AtomG* __restrict__ at, int natom, int n1, int n2, int n3, double h1,
+                                    double h2, double h3, double L1, double L2, double L3, double* __restrict__ b,
+                                    double* __restrict__ sad) {
+    const long long ng = (long long)n1 * n2 * n3;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(g % n1), j = (int)((g / n1) % n2), k = (int)(g / ((long long)n1 * n2));
+        const double x = i * h1, y = j * h2, z = k * h3;
+        double sb = 0.0, ss = 0.0;
+        for (int a = 0; a < natom; ++a) {
+            sb += image_sum(x, y, z, at[a].pos, L1, L2, L3, at[a].amp_b, at[a].w_b, at[a].cut_b);
+            ss += image_sum(x, y, z, at[a].pos, L1, L2, L3, at[a].amp_s, at[a].w_s, at[a].cut_s);
+        }
+        b[g] = sb;
+        sad[g] = ss;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// reductions: deterministic two-stage sums of several dot products
+// ---------------------------------------------------------------------------------------
+template <int K>
+__global__ void multidot_kernel(const double* const* __restrict__ A, const double* const* __restrict__ B, long long n,
+                                double* __restrict__ part) {
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (A[k]) acc[k] = fma(A[k][i], B[k][i], acc[k]);
+    }
+    __shared__ double sh[K][RB / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double v = acc[k];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double v = 0.0;
+        for (int w = 0; w < RB / 32; ++w) v += sh[threadIdx.x][w];
+        part[(long long)blockIdx.x * K + threadIdx.x] = v;
+    }
+}
+
+template <int K>
+__global__ void multidot_finish_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= K) return;
+    double v = 0.0;
+    for (int b = 0; b < nblk; ++b) v += part[(long long)b * K + k];
+    out[k] = v;
+}
+
+// ---------------------------------------------------------------------------------------
+// LDA (Perdew & Zunger 1981): PZ81 correlation, Dirac exchange, von Barth-Hedin f(zeta)
+// ---------------------------------------------------------------------------------------
+struct PZ {
+    double g, b1, b2, A, B, C, D;
+};
+__device__ __forceinline__ void pz_phase(double rs, const PZ& p, double& eps, double& mu) {
+    if (rs >= 1.0) {
+        const double s = sqrt(rs);
+        const double den = 1.0 + p.b1 * s + p.b2 * rs;
+        eps = p.g / den;
+        mu = eps * (1.0 + 7.0 / 6.0 * p.b1 * s + 4.0 / 3.0 * p.b2 * rs) / den;
+    } else {
+        const double lr = log(rs);
+        eps = p.A * lr + p.B + p.C * rs * lr + p.D * rs;
+        mu = p.A * lr + (p.B - p.A / 3.0) + 2.0 / 3.0 * p.C * rs * lr + (2.0 * p.D - p.C) / 3.0 * rs;
+    }
+}
+
+__global__ void lda_kernel(int nspin, const double* __restrict__ rho, double* __restrict__ exc,
+                           double* __restrict__ vxc, long long n) {
+    const PZ U{-0.1423, 1.0529, 0.3334, 0.0311, -0.048, 0.0020, -0.0116};
+    const PZ P{-0.0843, 1.3981, 0.2611, 0.01555, -0.0269, 0.0007, -0.0048};
+    const double floor_ = 1e-14;
+    const double cx = -0.75 * cbrt(3.0 / M_PI);
+    const double fden = pow(2.0, 4.0 / 3.0) - 2.0;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+        if (nspin == 1) {
+            const double r = fmax(rho[g], floor_);
+            const double ex = cx * cbrt(r);
+            const double rs = cbrt(3.0 / (4.0 * M_PI * r));
+            double ec, vc;
+            pz_phase(rs, U, ec, vc);
+            exc[g] = ex + ec;
+            vxc[g] = 4.0 / 3.0 * ex + vc;
+        } else {
+            const double ru = rho[g], rd = rho[n + g];
+            const double r = fmax(ru + rd, floor_);
+            const double z = fmin(1.0, fmax(-1.0, (ru - rd) / r));
+            const double exu = cx * cbrt(r);
+            const double opz = 1.0 + z, omz = 1.0 - z;
+            const double c_opz = cbrt(opz), c_omz = cbrt(omz);
+            const double ex = exu * 0.5 * (opz * c_opz + omz * c_omz);
+            const double rs = cbrt(3.0 / (4.0 * M_PI * r));
+            double eu, mu_u, ep, mu_p;
+            pz_phase(rs, U, eu, mu_u);
+            pz_phase(rs, P, ep, mu_p);
+            const double f = (opz * c_opz + omz * c_omz - 2.0) / fden;
+            const double df = 4.0 / 3.0 * (c_opz - c_omz) / fden;
+            const double ec = eu + f * (ep - eu);
+            const double vcc = mu_u + f * (mu_p - mu_u);
+            exc[g] = ex + ec;
+            vxc[g] = 4.0 / 3.0 * exu * c_opz + vcc + (ep - eu) * df * (1.0 - z);
+            vxc[n + g] = 4.0 / 3.0 * exu * c_omz + vcc + (ep - eu) * df * (-1.0 - z);
+        }
+    }
+}
+
+__global__ void veff_kernel(int nspin, const double* __restrict__ phi, const double* __restrict__ vxc,
+                            double* __restrict__ veff, float* __restrict__ veff32, long long n) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x)
+        for (int s = 0; s < nspin; ++s) {
+            const double v = phi[g] + vxc[s * n + g];
+            veff[s * n + g] = v;
+            veff32[s * n + g] = (float)v;
+        }
+}
+
+// ---------------------------------------------------------------------------------------
+// elementwise helpers
+// ---------------------------------------------------------------------------------------
+__global__ void axpby_kernel(double* __restrict__ y, const double* __restrict__ x, double a, double b, long long n) {
+    // y = a*x + b*y
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+__global__ void to_float_grid_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+__global__ void sum_spins_plus_kernel(const double* __restrict__ rho, int nspin, const double* __restrict__ add,
+                                      double* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double s = add ? add[i] : 0.0;
+        for (int k = 0; k < nspin; ++k) s += rho[k * n + i];
+        out[i] = s;
+    }
+}
+__global__ void add_scalar_kernel(double* __restrict__ y, const double* __restrict__ s, double scale, long long n) {
+    const double v = scale * s[0];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] += v;
+}
+
+// Anderson history push: X[slot] = x - xprev, F[slot] = c*f - fprev; xprev = x, fprev = c*f
+__global__ void anderson_push_kernel(const double* __restrict__ x, const double* __restrict__ f, double c,
+                                     double* __restrict__ xprev, double* __restrict__ fprev, double* __restrict__ Xs,
+                                     double* __restrict__ Fs, int have_prev, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double fi = c * f[i];
+        if (have_prev) {
+            Xs[i] = x[i] - xprev[i];
+            Fs[i] = fi - fprev[i];
+        }
+        xprev[i] = x[i];
+        fprev[i] = fi;
+    }
+}
+
+// x += a*c*f - sum_j gamma_j (X_j + a F_j)   (gamma in device memory, m terms)
+__global__ void anderson_update_kernel(double* __restrict__ x, const double* __restrict__ f, double c, double a,
+                                       const double* __restrict__ X, const double* __restrict__ F,
+                                       const int* __restrict__ slots, const double* __restrict__ gamma, int m,
+                                       long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = x[i] + a * c * f[i];
+        for (int j = 0; j < m; ++j) {
+            const long long o = (long long)slots[j] * n + i;
+            v -= gamma[j] * (X[o] + a * F[o]);
+        }
+        x[i] = v;
+    }
+}
+
+// Gram of the history: G[i][j] = F_i . F_j (i <= j), r_i = F_i . (c f), plus f.f; partials per block
+__global__ void anderson_gram_kernel(const double* __restrict__ F, const int* __restrict__ slots, int m,
+                                     const double* __restrict__ f, double c, long long n, double* __restrict__ part) {
+    constexpr int MM = 16;
+    const int nd = m * (m + 1) / 2 + m + 1;
+    double acc[MM * (MM + 1) / 2 + MM + 1];
+    for (int k = 0; k < nd; ++k) acc[k] = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v[MM];
+        for (int j = 0; j < m; ++j) v[j] = F[(long long)slots[j] * n + i];
+        const double fi = c * f[i];
+        int k = 0;
+        for (int a = 0; a < m; ++a)
+            for (int b = a; b < m; ++b) acc[k++] += v[a] * v[b];
+        for (int a = 0; a < m; ++a) acc[k++] += v[a] * fi;
+        acc[k] += fi * fi;
+    }
+    __shared__ double sh[RB / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < nd; ++k) {
+        double v = acc[k];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[warp] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < RB / 32; ++w) s += sh[w];
+            part[(long long)blockIdx.x * nd + k] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// sum partials, solve (F^T F) gamma = F^T f by Gaussian elimination with partial pivoting
+__global__ void anderson_solve_kernel(const double* __restrict__ part, int nblk, int m, double* __restrict__ gamma,
+                                      double* __restrict__ ff) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    constexpr int MM = 16;
+    const int nd = m * (m + 1) / 2 + m + 1;
+    double s[MM * (MM + 1) / 2 + MM + 1];
+    for (int k = 0; k < nd; ++k) {
+        double v = 0.0;
+        for (int b = 0; b < nblk; ++b) v += part[(long long)b * nd + k];
+        s[k] = v;
+    }
+    double G[MM][MM + 1];
+    int k = 0;
+    for (int a = 0; a < m; ++a)
+        for (int b = a; b < m; ++b) {
+            G[a][b] = s[k];
+            G[b][a] = s[k];
+            ++k;
+        }
+    for (int a = 0; a < m; ++a) G[a][m] = s[k++];
+    ff[0] = s[k];
+    for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < m; ++r)
+            if (fabs(G[r][col]) > fabs(G[piv][col])) piv = r;
+        if (piv != col)
+            for (int q = 0; q <= m; ++q) {
+                double t = G[col][q];
+                G[col][q] = G[piv][q];
+                G[piv][q] = t;
+            }
+        const double d = G[col][col];
+        for (int r = col + 1; r < m; ++r) {
+            const double fct = d != 0.0 ? G[r][col] / d : 0.0;
+            for (int q = col; q <= m; ++q) G[r][q] -= fct * G[col][q];
+        }
+    }
+    for (int r = m - 1; r >= 0; --r) {
+        double v = G[r][m];
+        for (int q = r + 1; q < m; ++q) v -= G[r][q] * gamma[q];
+        gamma[r] = G[r][r] != 0.0 ? v / G[r][r] : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// density from orbitals (Eq. 2): rho[g] += weight * sum_n occ[n] |X[g,n]|^2 / dV
+// ---------------------------------------------------------------------------------------
+template <int KIND>  // 0 FP64 real, 1 FP64 complex, 2 FP32 paired real, 3 FP32 complex
+__global__ void density_kernel(const void* __restrict__ X, const double* __restrict__ occ, int ncol, double scale,
+                               long long ng, double* __restrict__ rho) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        if (KIND == 0) {
+            const double* x = (const double*)X;
+            for (int n = 0; n < ncol; ++n) {
+                const double v = x[(long long)n * ng + g];
+                s += occ[n] * v * v;
+            }
+        } else if (KIND == 1) {
+            const double2* x = (const double2*)X;
+            for (int n = 0; n < ncol; ++n) {
+                const double2 v = x[(long long)n * ng + g];
+                s += occ[n] * (v.x * v.x + v.y * v.y);
+            }
+        } else if (KIND == 2) {
+            const float2* x = (const float2*)X;
+            for (int p = 0; p < ncol / 2; ++p) {
+                const float2 v = x[(long long)p * ng + g];
+                s += occ[2 * p] * (double)v.x * v.x + occ[2 * p + 1] * (double)v.y * v.y;
+            }
+        } else {
+            const float2* x = (const float2*)X;
+            for (int n = 0; n < ncol; ++n) {
+                const float2 v = x[(long long)n * ng + g];
+                s += occ[n] * ((double)v.x * v.x + (double)v.y * v.y);
+            }
+        }
+        rho[g] += scale * s;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Fermi level: bisection on sum_{s,k} w_k sum_n g = N_e, g = f_s / (1 + exp((e - mu)/kT))
+// one CTA; writes occ, out[0] = mu, out[1] = -TS, out[2] = band energy sum w g e
+// ---------------------------------------------------------------------------------------
+__global__ void fermi_kernel(const double* __restrict__ eig, const double* __restrict__ kw, int nspin, int nk, int ns,
+                             double nelec, double kT, double fs, double* __restrict__ occ, double* __restrict__ out) {
+    __shared__ double red[1024 / 32];
+    __shared__ double lo_s, hi_s;
+    const int total = nspin * nk * ns;
+    double emin = 1e300, emax = -1e300;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        emin = fmin(emin, eig[i]);
+        emax = fmax(emax, eig[i]);
+    }
+    auto block_reduce = [&](double v, int op) -> double {  // op 0 sum, 1 min, 2 max
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int off = 16; off > 0; off >>= 1) {
+            const double o = __shfl_down_sync(0xffffffffu, v, off);
+            v = op == 0 ? v + o : (op == 1 ? fmin(v, o) : fmax(v, o));
+        }
+        __syncthreads();
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        double r = red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            r = op == 0 ? r + red[w] : (op == 1 ? fmin(r, red[w]) : fmax(r, red[w]));
+        return r;
+    };
+    emin = block_reduce(emin, 1);
+    emax = block_reduce(emax, 2);
+    if (threadIdx.x == 0) {
+        lo_s = emin - 50.0 * kT - 1.0;
+        hi_s = emax + 50.0 * kT + 1.0;
+    }
+    __syncthreads();
+    for (int it = 0; it < 200; ++it) {
+        const double lo = lo_s, hi = hi_s;
+        const double mid = 0.5 * (lo + hi);
+        double cnt = 0.0;
+        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+            const int k = (i / ns) % nk;
+            cnt += kw[k] * fs * 0.5 * (1.0 - tanh(0.5 * (eig[i] - mid) / kT));
+        }
+        cnt = block_reduce(cnt, 0);
+        if (threadIdx.x == 0) {
+            if (cnt < nelec) lo_s = mid;
+            else hi_s = mid;
+        }
+        __syncthreads();
+        if (hi_s - lo_s < 1e-15 * fmax(1.0, fabs(mid))) break;
+    }
+    const double mu = 0.5 * (lo_s + hi_s);
+    double ts = 0.0, eb = 0.0;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int k = (i / ns) % nk;
+        const double g = fs * 0.5 * (1.0 - tanh(0.5 * (eig[i] - mu) / kT));
+        occ[i] = g;
+        const double f = g / fs;
+        double t = 0.0;
+        if (f > 0.0) t += f * log(f);
+        if (f < 1.0) t += (1.0 - f) * log(1.0 - f);
+        ts += kw[k] * fs * kT * t;
+        eb += kw[k] * g * eig[i];
+    }
+    ts = block_reduce(ts, 0);
+    eb = block_reduce(eb, 0);
+    if (threadIdx.x == 0) {
+        out[0] = mu;
+        out[1] = ts;
+        out[2] = eb;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// forces
+// ---------------------------------------------------------------------------------------
+// local part per atom: -dV sum_x (x - R - T)/r_loc^2 b_a(x - R - T) phi(x); one CTA per atom
+__global__ void force_local_kernel(const AtomG* __restrict__ at, int n1, int n2, int n3, double h1, double h2,
+                                   double h3, double L1, double L2, double L3, double dV,
+                                   const double* __restrict__ phi, double* __restrict__ F) {
+    const int a = blockIdx.x;
+    const AtomG A = at[a];
+    const double cut = A.cut_b;
+    int lo[3], dim[3];
+    const double h[3] = {h1, h2, h3};
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = (int)ceil((A.pos[d] - cut) / h[d]);
+        dim[d] = (int)floor((A.pos[d] + cut) / h[d]) - lo[d] + 1;
+    }
+    const long long total = (long long)dim[0] * dim[1] * dim[2];
+    double acc[3] = {0, 0, 0};
+    const double inv = 1.0 / (2.0 * A.w_b * A.w_b);
+    for (long long p = threadIdx.x; p < total; p += blockDim.x) {
+        const int ix = (int)(p % dim[0]), iy = (int)((p / dim[0]) % dim[1]), iz = (int)(p / ((long long)dim[0] * dim[1]));
+        const int I[3] = {lo[0] + ix, lo[1] + iy, lo[2] + iz};
+        const double dx = I[0] * h1 - A.pos[0], dy = I[1] * h2 - A.pos[1], dz = I[2] * h3 - A.pos[2];
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 > cut * cut) continue;
+        const int g0 = ((I[0] % n1) + n1) % n1, g1 = ((I[1] % n2) + n2) % n2, g2 = ((I[2] % n3) + n3) % n3;
+        const double ph = phi[((long long)g2 * n2 + g1) * n1 + g0];
+        const double bv = A.amp_b * exp(-r2 * inv);
+        const double s = bv * ph / (A.w_b * A.w_b);
+        acc[0] += dx * s;
+        acc[1] += dy * s;
+        acc[2] += dz * s;
+    }
+    __shared__ double sh[3][RB / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = 0; d < 3; ++d) {
+        double v = acc[d];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[d][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0.0;
+        for (int w = 0; w < RB / 32; ++w) v += sh[threadIdx.x][w];
+        F[3 * a + threadIdx.x] -= dV * v;
+        (void)L1;
+        (void)L2;
+        (void)L3;
+    }
+}
+
+// nonlocal part per atom: C_n = sum_j conj(beta_j) X[j,n], D_nd = sum_j conj(dbeta_j/dR_d) X[j,n]
+// F_d -= w_k dV E_kb sum_n g_n 2 Re(conj(C_n) D_nd); FP64 blocks (real or complex)
+template <bool CPLX>
+__global__ void force_nl_kernel(const int* __restrict__ cnt, const int* __restrict__ idx, const int* __restrict__ img,
+                                const double* __restrict__ val, int cap, const double* __restrict__ X, int ncol,
+                                long long ng, const double* __restrict__ occ, double wk, const double* __restrict__ gamma,
+                                const double* __restrict__ apos, const double* __restrict__ rp2, int n1, int n2,
+                                double h1, double h2, double h3, double* __restrict__ F) {
+    const int a = blockIdx.x;
+    const int m = cnt[a];
+    const double R[3] = {apos[3 * a], apos[3 * a + 1], apos[3 * a + 2]};
+    double fsum[3] = {0, 0, 0};
+    __shared__ double sh[8][RB / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int n = 0; n < ncol; ++n) {
+        double c[2] = {0, 0}, d[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const long long e = (long long)a * cap + j;
+            const int g = idx[e];
+            const int pk = img[e];
+            const int t0 = (pk & 1023) - 512, t1 = ((pk >> 10) & 1023) - 512, t2 = ((pk >> 20) & 1023) - 512;
+            const int gx = g % n1, gy = (g / n1) % n2, gz = g / (n1 * n2);
+            // unwrapped box point I = g + t n;   displacement x_I - R
+            const double disp[3] = {(gx + (double)t0 * n1) * h1 - R[0], (gy + (double)t1 * n2) * h2 - R[1],
+                                    (gz + (double)t2 * (ng / ((long long)n1 * n2))) * h3 - R[2]};
+            double br, bi;
+            if (CPLX) {
+                br = val[2 * e];
+                bi = val[2 * e + 1];
+            } else {
+                br = val[e];
+                bi = 0.0;
+            }
+            double xr, xi;
+            if (CPLX) {
+                xr = X[2 * ((long long)n * ng + g)];
+                xi = X[2 * ((long long)n * ng + g) + 1];
+            } else {
+                xr = X[(long long)n * ng + g];
+                xi = 0.0;
+            }
+            // conj(beta) * x
+            const double pr = br * xr + bi * xi, pi = br * xi - bi * xr;
+            c[0] += pr;
+            c[1] += pi;
+            for (int q = 0; q < 3; ++q) {
+                const double s = disp[q] / rp2[a];
+                d[q][0] += s * pr;
+                d[q][1] += s * pi;
+            }
+        }
+        double vals[8] = {c[0], c[1], d[0][0], d[0][1], d[1][0], d[1][1], d[2][0], d[2][1]};
+        for (int k = 0; k < 8; ++k) {
+            double v = vals[k];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) sh[k][warp] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s[8];
+            for (int k = 0; k < 8; ++k) {
+                s[k] = 0.0;
+                for (int w = 0; w < RB / 32; ++w) s[k] += sh[k][w];
+            }
+            for (int q = 0; q < 3; ++q) fsum[q] += occ[n] * 2.0 * (s[0] * s[2 + 2 * q] + s[1] * s[3 + 2 * q]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 3; ++q) F[3 * a + q] -= wk * gamma[a] * fsum[q];
+}
+
+inline unsigned nblocks(long long n, int bs = 256) {
+    return (unsigned)std::min<long long>((n + bs - 1) / bs, 152LL * 16);
+}
+
+std::vector<AtomG> atom_g(sdft_ctx* c) {
+    std::vector<AtomG> at(c->natom);
+    for (int a = 0; a < c->natom; ++a) {
+        const sdft_pseudo& s = c->species[c->types[a]];
+        for (int d = 0; d < 3; ++d) at[a].pos[d] = c->pos[3 * a + d];
+        at[a].amp_b = -s.Z * std::pow(2.0 * M_PI * s.r_loc * s.r_loc, -1.5);
+        at[a].w_b = s.r_loc;
+        at[a].cut_b = 10.0 * s.r_loc;
+        at[a].amp_s = s.Z * std::pow(2.0 * M_PI * s.sad_width * s.sad_width, -1.5);
+        at[a].w_s = s.sad_width;
+        at[a].cut_s = 10.0 * s.sad_width;
+    }
+    return at;
+}
+
+}  // namespace
+
+// out[k] = a_k . b_k for k < count (<= 8), synchronously to host
+void dots_host(sdft_ctx* c, int count, const double* const* a, const double* const* b, long long n, double* host_out) {
+    SDFT_REQUIRE(count >= 1 && count <= 8, SDFT_ERR_INVALID_ARG, "dots_host: count");
+    const double* pa[8] = {nullptr};
+    const double* pb[8] = {nullptr};
+    for (int k = 0; k < count; ++k) {
+        pa[k] = a[k];
+        pb[k] = b[k];
+    }
+    // pointer tables live in the small scalar area
+    const double** dA = (const double**)(c->scal + 1024);
+    const double** dB = (const double**)(c->scal + 1024 + 8);
+    double* part = c->scal + 2048;
+    double* out = c->scal + 1536;
+    SDFT_CUDA(cudaMemcpyAsync((void*)dA, pa, sizeof(pa), cudaMemcpyHostToDevice, c->stream));
+    SDFT_CUDA(cudaMemcpyAsync((void*)dB, pb, sizeof(pb), cudaMemcpyHostToDevice, c->stream));
+    const int nblk = 128;  // 128 blocks x 8 dots fits in the 2048-double partial area
+    multidot_kernel<8><<<nblk, RB, 0, c->stream>>>(dA, dB, n, part);
+    multidot_finish_kernel<8><<<1, 32, 0, c->stream>>>(part, nblk, out);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c, 2);
+    SDFT_CUDA(cudaMemcpyAsync(c->hscal, out, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < count; ++k) host_out[k] = c->hscal[k];
+}
+
+void build_pseudocharge_and_sad(sdft_ctx* c) {
+    std::vector<AtomG> at = atom_g(c);
+    AtomG* dat = (AtomG*)ctx_alloc(c, sizeof(AtomG) * std::max(1, c->natom));
+    SDFT_CUDA(cudaMemcpyAsync(dat, at.data(), sizeof(AtomG) * c->natom, cudaMemcpyHostToDevice, c->stream));
+    setup_fields_kernel<<<nblocks(c->ng), 256, 0, c->stream>>>(dat, c->natom, c->n[0], c->n[1], c->n[2], c->h[0],
+                                                              c->h[1], c->h[2], c->L[0], c->L[1], c->L[2], c->b,
+                                                              c->rho_sad);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+    // normalise the SAD density to N_e: sum rho = rho . 1
+    double* ones = c->work64;
+    SDFT_CUDA(cudaMemsetAsync(ones, 0, sizeof(double) * c->ng, c->stream));
+    c->hscal[0] = 1.0;
+    SDFT_CUDA(cudaMemcpyAsync(c->scal, c->hscal, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    add_scalar_kernel<<<nblocks(c->ng), 256, 0, c->stream>>>(ones, c->scal, 1.0, c->ng);
+    count_launch(c);
+    const double* a[1] = {c->rho_sad};
+    const double* b[1] = {ones};
+    double s = 0.0;
+    dots_host(c, 1, a, b, c->ng, &s);
+    const double scale = c->nelec / (c->dV * s);
+    axpby_kernel<<<nblocks(c->ng), 256, 0, c->stream>>>(c->rho_sad, c->rho_sad, 0.0, scale, c->ng);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+void lda_device(sdft_ctx* c, int nspin, const double* rho, double* exc, double* vxc, size_t n) {
+    lda_kernel<<<nblocks((long long)n), 256, 0, c->stream>>>(nspin, rho, exc, vxc, (long long)n);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+// V_eff^s = phi + v_xc^s from rho_in (Poisson solved by the caller into c->phi)
+void veff_assemble(sdft_ctx* c) {
+    const int ns = c->opt.nspin;
+    double* vxc = c->work64 + 2 * c->ng;  // [nspin][ng]
+    lda_device(c, ns, c->rho_in, c->exc, vxc, (size_t)c->ng);
+    veff_kernel<<<nblocks(c->ng), 256, 0, c->stream>>>(ns, c->phi, vxc, c->veff, c->veff32, c->ng);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+void veff_to_float(sdft_ctx* c, int spin) {
+    const long long n = c->ng;
+    to_float_grid_kernel<<<nblocks(n), 256, 0, c->stream>>>(c->veff + spin * n, c->veff32 + spin * n, n);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+// ---------------------------------------------------------------------------------------
+// AAR Poisson (Pratapa, Suryanarayana & Pask 2016; Suryanarayana et al. 2019):
+// A = -L_h, Jacobi preconditioner, Richardson steps with omega, Anderson every p-th step.
+// ---------------------------------------------------------------------------------------
+int poisson_aar(sdft_ctx* c, const double* f, double* phi, double tol, int max_iter) {
+    const long long n = c->ng;
+    const double omega = 0.6, beta = 0.6;
+    const int m = 7, p = 6;
+    // workspace: rhs, r, xprev, fprev, X[m], F[m]
+    double* rhs = c->work64 + 0 * n;
+    double* r = c->work64 + 1 * n;
+    double* xprev = c->work64 + 4 * n;
+    double* fprev = c->work64 + 5 * n;
+    double* hist = c->work64 + 6 * n;  // 2*m vectors
+    double* Xs = hist;
+    double* Fs = hist + (long long)m * n;
+    double* gam = c->scal + 64;
+    int* slots = (int*)(c->scal + 96);
+    double* ffv = c->scal + 128;
+    double* part = c->scal + 4096;
+    // rhs = 4 pi (f - mean f); phi -= mean(phi)
+    {
+        double* ones = c->work64 + 3 * n;
+        SDFT_CUDA(cudaMemsetAsync(ones, 0, sizeof(double) * n, c->stream));
+        c->hscal[0] = 1.0;
+        SDFT_CUDA(cudaMemcpyAsync(c->scal, c->hscal, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        add_scalar_kernel<<<nblocks(n), 256, 0, c->stream>>>(ones, c->scal, 1.0, n);
+        const double* A[2] = {f, phi};
+        const double* B[2] = {ones, ones};
+        double s[2];
+        dots_host(c, 2, A, B, n, s);
+        SDFT_CUDA(cudaMemcpyAsync(rhs, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        c->hscal[0] = -s[0] / n;
+        c->hscal[1] = -s[1] / n;
+        SDFT_CUDA(cudaMemcpyAsync(c->scal, c->hscal, 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        add_scalar_kernel<<<nblocks(n), 256, 0, c->stream>>>(rhs, c->scal, 1.0, n);
+        add_scalar_kernel<<<nblocks(n), 256, 0, c->stream>>>(phi, c->scal + 1, 1.0, n);
+        axpby_kernel<<<nblocks(n), 256, 0, c->stream>>>(rhs, rhs, 0.0, 4.0 * M_PI, n);
+        SDFT_CUDA(cudaGetLastError());
+        count_launch(c, 5);
+    }
+    double bnorm2;
+    {
+        const double* A[1] = {rhs};
+        dots_host(c, 1, A, A, n, &bnorm2);
+    }
+    if (bnorm2 == 0.0) {
+        SDFT_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * n, c->stream));
+        return 0;
+    }
+    // Jacobi: diag(-L) = -(sum_d w0/h_d^2) = 2*c0 (c0 = -1/2 sum_d w0/h^2 > 0)
+    const double cj = 1.0 / (2.0 * c->coef.c0);
+    int count = 0, head = 0, it = 0;
+    int hslots[16];
+    for (it = 0; it < max_iter; ++it) {
+        // r = rhs - A phi = rhs + L phi  (stencil: alpha=-2 on -1/2 L, beta=-1 on rhs)
+        launch_cheb_step<double>(c, 0, phi, rhs, r, 1, nullptr, nullptr, -2.0, -1.0, 0.0);
+        // history push with f = cj * r
+        const int slot = head;
+        anderson_push_kernel<<<nblocks(n), 256, 0, c->stream>>>(phi, r, cj, xprev, fprev, Xs + (long long)slot * n,
+                                                                Fs + (long long)slot * n, it > 0, n);
+        count_launch(c);
+        if (it > 0) {
+            head = (head + 1) % m;
+            count = std::min(count + 1, m);
+        }
+        const bool anderson = ((it + 1) % p == 0) && count > 0;
+        if (anderson) {
+            for (int j = 0; j < count; ++j) hslots[j] = ((head - count + j) % m + m) % m;
+            std::memcpy(c->hscal + 512, hslots, sizeof(int) * 16);
+            SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 512, sizeof(int) * count, cudaMemcpyHostToDevice, c->stream));
+            const int nblk = 64;
+            anderson_gram_kernel<<<nblk, RB, 0, c->stream>>>(Fs, slots, count, r, cj, n, part);
+            anderson_solve_kernel<<<1, 32, 0, c->stream>>>(part, nblk, count, gam, ffv);
+            anderson_update_kernel<<<nblocks(n), 256, 0, c->stream>>>(phi, r, cj, beta, Xs, Fs, slots, gam, count, n);
+            SDFT_CUDA(cudaGetLastError());
+            count_launch(c, 3);
+            // convergence: ||r||^2 = ffv / cj^2
+            SDFT_CUDA(cudaMemcpyAsync(c->hscal, ffv, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            SDFT_CUDA(cudaStreamSynchronize(c->stream));
+            const double rn2 = c->hscal[0] / (cj * cj);
+            if (!std::isfinite(rn2)) throw Error{SDFT_ERR_NONFINITE, "Poisson residual is not finite"};
+            if (rn2 <= tol * tol * bnorm2) {
+                ++it;
+                break;
+            }
+        } else {
+            // Richardson: phi += omega * cj * r
+            axpby_kernel<<<nblocks(n), 256, 0, c->stream>>>(phi, r, omega * cj, 1.0, n);
+            SDFT_CUDA(cudaGetLastError());
+            count_launch(c);
+        }
+    }
+    if (it >= max_iter) return -it;
+    return it;
+}
+
+void density_accumulate(sdft_ctx* c, int precision, bool cplx, const void* X, const double* occ, int ncol,
+                        double weight, double* rho) {
+    const double scale = weight / c->dV;
+    const unsigned nb = nblocks(c->ng);
+    if (precision == SDFT_FP64) {
+        if (cplx) density_kernel<1><<<nb, 256, 0, c->stream>>>(X, occ, ncol, scale, c->ng, rho);
+        else density_kernel<0><<<nb, 256, 0, c->stream>>>(X, occ, ncol, scale, c->ng, rho);
+    } else {
+        if (cplx) density_kernel<3><<<nb, 256, 0, c->stream>>>(X, occ, ncol, scale, c->ng, rho);
+        else density_kernel<2><<<nb, 256, 0, c->stream>>>(X, occ, ncol, scale, c->ng, rho);
+    }
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+void fermi_device(sdft_ctx* c, const double* eig, double* occ, double* out) {
+    const int nk = c->opt.nkpt;
+    double* kw = c->scal + 256;
+    SDFT_CUDA(cudaMemcpyAsync(kw, c->kw.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, c->stream));
+    const double fs = c->opt.nspin == 1 ? 2.0 : 1.0;
+    fermi_kernel<<<1, 1024, 0, c->stream>>>(eig, kw, c->opt.nspin, nk, c->opt.nstates, c->nelec, c->opt.kT, fs, occ,
+                                            out);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+// Pulay mixing on rho_in (paper Sec. 2.1; Banerjee et al. 2016, Pratapa & Suryanarayana 2015):
+// f = rho_out - rho_in; linear step rho += beta f, or Pulay every period-th iteration.
+void pulay_update(sdft_ctx* c) {
+    const long long n = (long long)c->opt.nspin * c->ng;
+    const int m = c->opt.mix_hist;
+    double* f = c->work64;  // needs nspin*ng <= 2 ng: use work64[0 .. 2ng)
+    // f = rho_out - rho_in
+    SDFT_CUDA(cudaMemcpyAsync(f, c->rho_out, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    axpby_kernel<<<nblocks(n), 256, 0, c->stream>>>(f, c->rho_in, -1.0, 1.0, n);
+    count_launch(c);
+    const int slot = c->mix_head;
+    anderson_push_kernel<<<nblocks(n), 256, 0, c->stream>>>(c->rho_in, f, 1.0, c->mix_xprev, c->mix_fprev,
+                                                            c->mix_dx + (long long)slot * n,
+                                                            c->mix_df + (long long)slot * n, c->mix_k > 0, n);
+    count_launch(c);
+    if (c->mix_k > 0) {
+        c->mix_head = (c->mix_head + 1) % m;
+        c->mix_count = std::min(c->mix_count + 1, m);
+    }
+    const bool pulay = c->mix_k > 0 && c->mix_count > 0 && ((c->mix_k + 1) % c->opt.pulay_period == 0);
+    if (pulay) {
+        int hslots[16];
+        const int cnt = c->mix_count;
+        for (int j = 0; j < cnt; ++j) hslots[j] = ((c->mix_head - cnt + j) % m + m) % m;
+        int* slots = (int*)(c->scal + 160);
+        double* gam = c->scal + 192;
+        double* ffv = c->scal + 224;
+        double* part = c->scal + 4096;
+        std::memcpy(c->hscal + 640, hslots, sizeof(int) * 16);
+        SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 640, sizeof(int) * cnt, cudaMemcpyHostToDevice, c->stream));
+        const int nblk = 32;  // 32 x (m(m+1)/2 + m + 1) <= 12288 partials for m <= 16
+        anderson_gram_kernel<<<nblk, RB, 0, c->stream>>>(c->mix_df, slots, cnt, f, 1.0, n, part);
+        anderson_solve_kernel<<<1, 32, 0, c->stream>>>(part, nblk, cnt, gam, ffv);
+        anderson_update_kernel<<<nblocks(n), 256, 0, c->stream>>>(c->rho_in, f, 1.0, c->opt.mix_beta, c->mix_dx,
+                                                                  c->mix_df, slots, gam, cnt, n);
+        count_launch(c, 3);
+        if (c->opt.pulay_restart) {
+            c->mix_count = 0;
+        }
+    } else {
+        axpby_kernel<<<nblocks(n), 256, 0, c->stream>>>(c->rho_in, f, c->opt.mix_beta, 1.0, n);
+        count_launch(c);
+    }
+    SDFT_CUDA(cudaGetLastError());
+    c->mix_k += 1;
+}
+
+void forces_compute(sdft_ctx* c) {
+    const int na = c->natom;
+    c->forces.assign(3 * na, 0.0);
+    double* dF = c->scal + 3072;  // up to 341 atoms
+    SDFT_REQUIRE(3 * na <= 1024, SDFT_ERR_INVALID_ARG, "forces: too many atoms for the scalar area");
+    for (int i = 0; i < 3 * na; ++i) c->hscal[i] = -c->dEsc[i];
+    SDFT_CUDA(cudaMemcpyAsync(dF, c->hscal, sizeof(double) * 3 * na, cudaMemcpyHostToDevice, c->stream));
+    std::vector<AtomG> at = atom_g(c);
+    AtomG* dat = (AtomG*)ctx_alloc(c, sizeof(AtomG) * std::max(1, na));
+    SDFT_CUDA(cudaMemcpyAsync(dat, at.data(), sizeof(AtomG) * na, cudaMemcpyHostToDevice, c->stream));
+    force_local_kernel<<<na, RB, 0, c->stream>>>(dat, c->n[0], c->n[1], c->n[2], c->h[0], c->h[1], c->h[2], c->L[0],
+                                                 c->L[1], c->L[2], c->dV, c->phi, dF);
+    count_launch(c);
+    std::vector<double> rp2(na);
+    for (int a = 0; a < na; ++a) rp2[a] = std::pow(c->species[c->types[a]].r_proj, 2);
+    double* d_rp2 = (double*)ctx_alloc(c, sizeof(double) * std::max(1, na));
+    double* d_pos = (double*)ctx_alloc(c, sizeof(double) * 3 * std::max(1, na));
+    SDFT_CUDA(cudaMemcpyAsync(d_rp2, rp2.data(), sizeof(double) * na, cudaMemcpyHostToDevice, c->stream));
+    SDFT_CUDA(cudaMemcpyAsync(d_pos, c->pos.data(), sizeof(double) * 3 * na, cudaMemcpyHostToDevice, c->stream));
+    for (const Problem& P : c->probs) {
+        const KBTables& T = c->kb[P.kpt];
+        const void* X = c->opt.precision == SDFT_FP64 ? P.X : P.X64;
+        SDFT_REQUIRE(X != nullptr, SDFT_ERR_INVALID_ARG, "forces need FP64 orbitals");
+        const double wk = c->kw[P.kpt];
+        if (T.cplx)
+            force_nl_kernel<true><<<na, RB, 0, c->stream>>>(T.cnt, T.idx, T.img, T.val64, T.cap, (const double*)X,
+                                                           c->opt.nstates, c->ng, P.occ, wk, T.gamma, d_pos, d_rp2,
+                                                           c->n[0], c->n[1], c->h[0], c->h[1], c->h[2], dF);
+        else
+            force_nl_kernel<false><<<na, RB, 0, c->stream>>>(T.cnt, T.idx, T.img, T.val64, T.cap, (const double*)X,
+                                                            c->opt.nstates, c->ng, P.occ, wk, T.gamma, d_pos, d_rp2,
+                                                            c->n[0], c->n[1], c->h[0], c->h[1], c->h[2], dF);
+        count_launch(c);
+    }
+    SDFT_CUDA(cudaGetLastError());
+    SDFT_CUDA(cudaMemcpyAsync(c->hscal, dF, sizeof(double) * 3 * na, cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 3 * na; ++i) c->forces[i] = c->hscal[i];
+}
+
+}  // namespace sdft

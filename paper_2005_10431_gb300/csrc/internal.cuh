@@ -1,0 +1,233 @@
+// Internal declarations of the sdft library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sdft.h"
+
+namespace sdft {
+
+constexpr int FD_RADIUS = 6;
+constexpr int SCAL_DOUBLES = 16384;
+constexpr int MAX_KPT = 256;
+
+// ---------------------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------------------
+struct Error {
+    sdft_status code;
+    std::string msg;
+};
+
+#define SDFT_CUDA(call)                                                                     \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            throw ::sdft::Error{SDFT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+#define SDFT_REQUIRE(cond, code, text)                                                      \
+    do {                                                                                    \
+        if (!(cond)) throw ::sdft::Error{(code), (text)};                                   \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------
+// element types of orbital blocks
+// ---------------------------------------------------------------------------------------
+// E = float2 : SDFT_MIXED.  Real problems store two orbitals per element ("paired"),
+//              complex problems store (re, im) of one orbital.
+// E = double : SDFT_FP64 real.      E = double2 : SDFT_FP64 complex.
+template <typename E> struct Elem;
+template <> struct Elem<float2> { using S = float; static constexpr int lanes = 2; };
+template <> struct Elem<double> { using S = double; static constexpr int lanes = 1; };
+template <> struct Elem<double2> { using S = double; static constexpr int lanes = 2; };
+
+struct StencilCoef {
+    // -1/2 w_r / h_d^2 for r = 1..6 per axis; c0 = -1/2 sum_d w_0 / h_d^2
+    double cx[FD_RADIUS + 1], cy[FD_RADIUS + 1], cz[FD_RADIUS + 1];
+    double c0;
+};
+
+// Per-point KB scatter table and per-atom projection lists of one k-point.
+struct KBTables {
+    int natom = 0;
+    int cap = 0;              // entries reserved per atom
+    int* cnt = nullptr;       // [natom] support size
+    int* idx = nullptr;       // [natom*cap] grid index, ascending (z, y, x box order)
+    int* img = nullptr;       // [natom*cap] packed image vector t (3 x 10 bits, biased by 512)
+    double* val64 = nullptr;  // [natom*cap] real chi (double)  or [2*natom*cap] complex beta
+    float* val32 = nullptr;   // same in float
+    int S = 0;                // slots per grid point
+    int* pcnt = nullptr;      // [ng]
+    int* patom = nullptr;     // [S*ng]
+    double* pval64 = nullptr; // [S*ng] (x2 complex)
+    float* pval32 = nullptr;
+    double* gamma = nullptr;  // [natom] E_kb * dV
+    bool cplx = false;
+};
+
+struct Problem {              // one (spin, k) eigenproblem
+    int spin = 0, kpt = 0;
+    bool cplx = false;
+    void* X = nullptr;        // current orbitals (FP64 or MIXED storage)
+    void* X64 = nullptr;      // FP64 copy used by the final FP64 pass (MIXED)
+    double* eig = nullptr;    // [nstates]
+    double* occ = nullptr;    // [nstates]
+    double lower = 0, cutoff = 0, upper = 0;
+    bool have_bounds = false;
+};
+
+}  // namespace sdft
+
+struct sdft_ctx {
+    // geometry and options
+    int n[3] = {0, 0, 0};
+    double L[3] = {0, 0, 0}, h[3] = {0, 0, 0}, dV = 0;
+    long long ng = 0;
+    int natom = 0;
+    std::vector<double> pos;
+    std::vector<int> types;
+    std::vector<sdft_pseudo> species;
+    sdft_options opt{};
+    std::vector<double> kpts, kw;
+    double nelec = 0;
+    sdft::StencilCoef coef{};
+
+    cudaStream_t stream = nullptr;
+    sdft_alloc_fn alloc = nullptr;
+    sdft_free_fn release = nullptr;
+    void* alloc_user = nullptr;
+    std::vector<void*> owned;
+    cusolverDnHandle_t solver = nullptr;
+    uint64_t launches = 0;
+
+    // grid fields (FP64)
+    double* b = nullptr;          // pseudocharge
+    double* rho_sad = nullptr;    // SAD density (total)
+    double* rho_user = nullptr;   // user guess [nspin][ng]
+    double* rho_in = nullptr;     // [nspin][ng]
+    double* rho_out = nullptr;    // [nspin][ng]
+    double* phi = nullptr;        // electrostatic potential
+    double* veff = nullptr;       // [nspin][ng]
+    float* veff32 = nullptr;      // [nspin][ng]
+    double* exc = nullptr;        // eps_xc
+    double* work64 = nullptr;     // [28*ng] grid scratch (Poisson, mixing, energies, Lanczos)
+    // small device scalars / reductions [SCAL_DOUBLES], regions:
+    //   [0,8) temporaries  [8,16) Fermi (mu, -TS, band energy)  [64,256) Anderson/Pulay small data
+    //   [256,512) k-weights  [1024,1040) dot pointer tables  [1536,1544) dot results
+    //   [2048,3072) dot partials  [3072,4096) forces  [4096,16384) Anderson Gram partials
+    double* scal = nullptr;
+    double* hscal = nullptr;      // pinned host mirror [SCAL_DOUBLES]
+
+    std::vector<sdft::KBTables> kb;   // per k-point
+    std::vector<sdft::Problem> probs; // [spin*nkpt + k]
+
+    // block scratch (largest storage kind): 3 filter buffers + H Y
+    size_t block_bytes = 0;
+    void* blk[4] = {nullptr, nullptr, nullptr, nullptr};
+    double* Ms = nullptr;         // nstates^2 (x2 complex)
+    double* Hs = nullptr;
+    double* part = nullptr;       // split-K partials
+    size_t part_elems = 0;
+    double* dscale = nullptr;     // equilibration
+    double* eigtmp = nullptr;
+    void* solver_work = nullptr;
+    int solver_lwork = 0;
+    int* dinfo = nullptr;
+    void* Q32 = nullptr;          // rotation matrix in the block precision
+    float* C32 = nullptr;         // KB coefficients [ncol * natom] (x2)
+    double* C64 = nullptr;
+
+    // mixing history
+    double* mix_dx = nullptr;     // [hist][nspin*ng]
+    double* mix_df = nullptr;
+    double* mix_xprev = nullptr;
+    double* mix_fprev = nullptr;
+    int mix_k = 0, mix_count = 0, mix_head = 0;
+    bool user_density = false;
+
+    // results
+    std::vector<sdft_iter_record> log;
+    std::vector<double> forces;
+    std::vector<double> eig_host, occ_host;
+    double mu = 0, ts = 0;
+    double E_self = 0, E_sc = 0;
+    std::vector<double> dEsc;     // natom*3
+
+    std::string last_error;
+};
+
+namespace sdft {
+
+// allocation through the context's callbacks
+void* ctx_alloc(sdft_ctx* c, size_t bytes);
+void ctx_free_all(sdft_ctx* c);
+inline void count_launch(sdft_ctx* c, int n = 1) { c->launches += n; }
+inline size_t block_elems_bytes(const sdft_ctx* c, int precision, bool cplx, int ncol) {
+    // bytes of an ngrid x ncol block in the storage kind of (precision, cplx)
+    size_t per = precision == SDFT_FP64 ? (cplx ? 16 : 8) : (cplx ? 8 : 4);
+    return per * (size_t)c->ng * (size_t)ncol;
+}
+
+// ---- stencil.cu ----------------------------------------------------------------------
+// Ynext = alpha*(H Y - c Y) - beta*Yprev  for `ncolE` element-columns (see Elem).
+// Yprev may be null (beta ignored).  V null: no local potential.  kbC null: no KB term.
+// kb must hold the per-point table of this k-point; kbC is [ncolE][natom] elements of the
+// (gamma-scaled) projection coefficients of Y.
+template <typename E>
+void launch_cheb_step(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, int ncolE,
+                      const typename Elem<E>::S* V, const E* kbC, double alpha, double beta,
+                      double shift, bool with_kinetic = true);
+// KB projection C[col][a] = gamma_a * sum_j conj(beta_a(j)) Y[j, col]
+template <typename E>
+void launch_kb_project(sdft_ctx* c, int kpt, const E* Y, E* C, int ncolE);
+
+// ---- kb.cu ---------------------------------------------------------------------------
+void build_kb_tables(sdft_ctx* c, int kpt);
+
+// ---- gridops.cu ----------------------------------------------------------------------
+void build_pseudocharge_and_sad(sdft_ctx* c);
+void lda_device(sdft_ctx* c, int nspin, const double* rho, double* exc, double* vxc, size_t n);
+void veff_assemble(sdft_ctx* c);
+void veff_to_float(sdft_ctx* c, int spin);
+void axpby_dev(sdft_ctx* c, double* y, const double* x, double a, double b, long long n);
+int poisson_aar(sdft_ctx* c, const double* f, double* phi, double tol, int max_iter);
+// reductions: out[i] = sum_g a_i[g] * b_i[g] (device scal), returned synchronously to host
+void dots_host(sdft_ctx* c, int count, const double* const* a, const double* const* b, long long n,
+               double* host_out);
+void fermi_device(sdft_ctx* c, const double* eig, double* occ, double* mu_ts_dev);
+void density_accumulate(sdft_ctx* c, int precision, bool cplx, const void* X, const double* occ,
+                        int ncol, double weight, double* rho);
+void pulay_update(sdft_ctx* c);
+void forces_compute(sdft_ctx* c);
+
+// ---- dense.cu ------------------------------------------------------------------------
+// M = Y^H Y, Hs = Y^H HY (FP64 results, column-major ncol x ncol, x2 for complex)
+void subspace_gram(sdft_ctx* c, int precision, bool cplx, const void* Y, const void* HY,
+                   double* M, double* Hs, int ncol);
+// solve Hs q = lambda M q (FP64); Q overwrites Hs; eig ascending; throws CHOLESKY on failure
+void generalized_eig(sdft_ctx* c, bool cplx, double* M, double* Hs, double* eig, int ncol);
+// X = Y Q (Q FP64 column-major)
+void rotate_block(sdft_ctx* c, int precision, bool cplx, const void* Y, const double* Q, void* X,
+                  int ncol);
+void convert_block(sdft_ctx* c, bool cplx, int from_precision, const void* src, void* dst, int ncol);
+
+// ---- scf.cu --------------------------------------------------------------------------
+void chebyshev_filter(sdft_ctx* c, int kpt, int precision, const void* X, void* Y, int ncol,
+                      int degree, double a, double b, double a0, const double* veff64,
+                      const float* veff32);
+void apply_h(sdft_ctx* c, int kpt, int precision, const void* X, void* Y, int ncol,
+             const double* veff64, const float* veff32);
+void rayleigh_ritz(sdft_ctx* c, int kpt, int precision, const void* Y, void* X, double* eig,
+                   int ncol, const double* veff64, const float* veff32);
+void lanczos(sdft_ctx* c, int spin, int kpt, int steps, double* lower, double* upper);
+sdft_status run_scf(sdft_ctx* c, sdft_result* out);
+void reset_state(sdft_ctx* c);
+void seed_orbitals(sdft_ctx* c, int precision, bool cplx, void* X, int ncol, uint64_t seed);
+
+}  // namespace sdft

@@ -1,0 +1,501 @@
+// CheFSI inside the SCF loop (paper Sec. 2.1):
+//  * spectrum bounds by Lanczos, then per SCF iteration a degree-m Chebyshev filter and a
+//    Rayleigh-Ritz step for every (spin, k) problem, several filter passes in the first
+//    SCF iteration;
+//  * Fermi level, density (Eq. 2), Harris-Foulkes free energy, SCF error, Pulay mixing;
+//  * for SDFT_MIXED, an optional FP64 filter + Rayleigh-Ritz pass at the end.
+// Host code drives the iteration; every grid- or block-sized step runs in this library's
+// kernels on the context's stream.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+namespace sdft {
+
+// ---------------------------------------------------------------------------------------
+// counter-based initial orbitals: splitmix64 (Steele, Lea & Flood 2014), uniform in [-0.5, 0.5)
+// value (g, n) of stream s = top 53 bits of splitmix64(s * 2^32 + n*ngrid + g)
+// ---------------------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    unsigned long long z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ double uniform_counter(unsigned long long seed, unsigned long long i) {
+    const unsigned long long z = splitmix64(((seed & 0xffffffffULL) << 32) + i);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+}
+
+__global__ void seed_kernel(int kind, void* __restrict__ X, int ncol, long long ng, unsigned long long seed) {
+    const long long total = (long long)ncol * ng;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int n = (int)(e / ng);
+        const long long g = e - (long long)n * ng;
+        const double re = uniform_counter(seed, (unsigned long long)e);
+        if (kind == 0) {
+            ((double*)X)[e] = re;
+        } else if (kind == 1) {
+            const double im = uniform_counter(seed + 0x5BD1, (unsigned long long)e);
+            ((double2*)X)[e] = make_double2(re, im);
+        } else if (kind == 2) {
+            ((float*)X)[(((long long)(n >> 1)) * ng + g) * 2 + (n & 1)] = (float)re;
+        } else {
+            const double im = uniform_counter(seed + 0x5BD1, (unsigned long long)e);
+            ((float2*)X)[e] = make_float2((float)re, (float)im);
+        }
+    }
+}
+
+__global__ void spin_split_kernel(const double* __restrict__ rho, int nspin, double moment, double* __restrict__ out,
+                                  long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (nspin == 1) {
+            out[i] = rho[i];
+        } else {
+            out[i] = 0.5 * rho[i] * (1.0 + moment);
+            out[n + i] = 0.5 * rho[i] * (1.0 - moment);
+        }
+    }
+}
+
+__global__ void lincomb_kernel(double* __restrict__ y, const double* __restrict__ x, const double* __restrict__ z,
+                               double a, double b, double cc, long long n) {
+    // y = a*y + b*x + cc*z
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = a * y[i] + b * x[i];
+        if (z) v += cc * z[i];
+        y[i] = v;
+    }
+}
+
+__global__ void sum_spins_kernel(const double* __restrict__ rho, int nspin, const double* __restrict__ add,
+                                 double* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double s = add ? add[i] : 0.0;
+        for (int k = 0; k < nspin; ++k) s += rho[k * n + i];
+        out[i] = s;
+    }
+}
+
+inline unsigned nb(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16); }
+inline int kind_of(int precision, bool cplx) { return precision == SDFT_FP64 ? (cplx ? 1 : 0) : (cplx ? 3 : 2); }
+inline double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ---- typed filter / H application -------------------------------------------------------
+template <typename E>
+void filter_typed(sdft_ctx* c, int kpt, const E* X, E* Y, E* T1, E* T2, int ncolE, int m, double a, double b,
+                  double a0, const typename Elem<E>::S* V, E* C) {
+    const double e = 0.5 * (b - a), cc = 0.5 * (b + a);
+    const double sigma1 = e / (a0 - cc);
+    double sigma = sigma1;
+    E* ring[3] = {T1, T2, Y};
+    auto slot = [&](int k) -> E* { return ring[(((2 - (m - k)) % 3) + 3) % 3]; };
+    const bool kb = c->kb[kpt].S > 0;
+    for (int k = 1; k <= m; ++k) {
+        const E* cur = k == 1 ? X : slot(k - 1);
+        const E* prev = k == 1 ? nullptr : (k == 2 ? X : slot(k - 2));
+        if (kb) launch_kb_project<E>(c, kpt, cur, C, ncolE);
+        double alpha, beta = 0.0;
+        if (k == 1) {
+            alpha = sigma1 / e;
+        } else {
+            const double sigma2 = 1.0 / (2.0 / sigma1 - sigma);
+            alpha = 2.0 * sigma2 / e;
+            beta = sigma * sigma2;
+            sigma = sigma2;
+        }
+        launch_cheb_step<E>(c, kpt, cur, prev, slot(k), ncolE, V, kb ? C : nullptr, alpha, beta, cc);
+    }
+}
+
+template <typename E>
+void apply_h_typed(sdft_ctx* c, int kpt, const E* X, E* Y, int ncolE, const typename Elem<E>::S* V, E* C) {
+    const bool kb = c->kb[kpt].S > 0;
+    if (kb) launch_kb_project<E>(c, kpt, X, C, ncolE);
+    launch_cheb_step<E>(c, kpt, X, nullptr, Y, ncolE, V, kb ? C : nullptr, 1.0, 0.0, 0.0);
+}
+
+// pick the two filter temporaries among the context's block buffers, distinct from Y/X
+void pick_temps(sdft_ctx* c, const void* X, const void* Y, void** t1, void** t2) {
+    int got = 0;
+    for (int i = 0; i < 4 && got < 2; ++i) {
+        if (c->blk[i] == X || c->blk[i] == Y) continue;
+        if (got == 0) *t1 = c->blk[i];
+        else *t2 = c->blk[i];
+        ++got;
+    }
+    SDFT_REQUIRE(got == 2, SDFT_ERR_INVALID_ARG, "no free block buffers for the filter");
+}
+
+// tridiagonal (alpha, beta) extreme eigenvalues by Sturm-sequence bisection
+double sturm_count(const std::vector<double>& al, const std::vector<double>& be, double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (size_t i = 0; i < al.size(); ++i) {
+        const double b2 = i > 0 ? be[i - 1] * be[i - 1] : 0.0;
+        q = al[i] - x - (i > 0 ? b2 / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+double tridiag_eig(const std::vector<double>& al, const std::vector<double>& be, int which) {
+    // which-th smallest eigenvalue (0-based)
+    double lo = 1e300, hi = -1e300;
+    for (size_t i = 0; i < al.size(); ++i) {
+        const double r = (i > 0 ? std::fabs(be[i - 1]) : 0.0) + (i + 1 < al.size() ? std::fabs(be[i]) : 0.0);
+        lo = std::min(lo, al[i] - r);
+        hi = std::max(hi, al[i] + r);
+    }
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(al, be, mid) > which) hi = mid;
+        else lo = mid;
+        if (hi - lo < 1e-15 * std::max(1.0, std::fabs(mid))) break;
+    }
+    return 0.5 * (lo + hi);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+void axpby_dev(sdft_ctx* c, double* y, const double* x, double a, double b, long long n) {
+    lincomb_kernel<<<nb(n), 256, 0, c->stream>>>(y, x, nullptr, b, a, 0.0, n);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+void seed_orbitals(sdft_ctx* c, int precision, bool cplx, void* X, int ncol, uint64_t seed) {
+    seed_kernel<<<nb((long long)ncol * c->ng), 256, 0, c->stream>>>(kind_of(precision, cplx), X, ncol, c->ng, seed);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+uint64_t problem_seed(const sdft_ctx* c, int s, int k) {
+    return c->opt.seed * 4099ULL + (uint64_t)s * (uint64_t)c->opt.nkpt + (uint64_t)k;
+}
+
+void chebyshev_filter(sdft_ctx* c, int kpt, int precision, const void* X, void* Y, int ncol, int degree, double a,
+                      double b, double a0, const double* veff64, const float* veff32) {
+    SDFT_REQUIRE(degree >= 1, SDFT_ERR_INVALID_ARG, "degree must be >= 1");
+    SDFT_REQUIRE(b > a && a > a0, SDFT_ERR_INVALID_ARG, "filter bounds must satisfy a0 < a < b");
+    void *t1 = nullptr, *t2 = nullptr;
+    pick_temps(c, X, Y, &t1, &t2);
+    const bool cplx = c->kb[kpt].cplx;
+    if (precision == SDFT_FP64) {
+        if (cplx)
+            filter_typed<double2>(c, kpt, (const double2*)X, (double2*)Y, (double2*)t1, (double2*)t2, ncol, degree, a,
+                                  b, a0, veff64, (double2*)c->C64);
+        else
+            filter_typed<double>(c, kpt, (const double*)X, (double*)Y, (double*)t1, (double*)t2, ncol, degree, a, b,
+                                 a0, veff64, c->C64);
+    } else {
+        const int ncolE = cplx ? ncol : ncol / 2;
+        filter_typed<float2>(c, kpt, (const float2*)X, (float2*)Y, (float2*)t1, (float2*)t2, ncolE, degree, a, b, a0,
+                             veff32, (float2*)c->C32);
+    }
+}
+
+void apply_h(sdft_ctx* c, int kpt, int precision, const void* X, void* Y, int ncol, const double* veff64,
+             const float* veff32) {
+    const bool cplx = c->kb[kpt].cplx;
+    if (precision == SDFT_FP64) {
+        if (cplx) apply_h_typed<double2>(c, kpt, (const double2*)X, (double2*)Y, ncol, veff64, (double2*)c->C64);
+        else apply_h_typed<double>(c, kpt, (const double*)X, (double*)Y, ncol, veff64, c->C64);
+    } else {
+        const int ncolE = cplx ? ncol : ncol / 2;
+        apply_h_typed<float2>(c, kpt, (const float2*)X, (float2*)Y, ncolE, veff32, (float2*)c->C32);
+    }
+}
+
+void rayleigh_ritz(sdft_ctx* c, int kpt, int precision, const void* Y, void* X, double* eig, int ncol,
+                   const double* veff64, const float* veff32) {
+    const bool cplx = c->kb[kpt].cplx;
+    void* HY = nullptr;
+    for (int i = 0; i < 4; ++i)
+        if (c->blk[i] != Y && c->blk[i] != X) {
+            HY = c->blk[i];
+            break;
+        }
+    SDFT_REQUIRE(HY != nullptr, SDFT_ERR_INVALID_ARG, "no free block buffer for H Y");
+    apply_h(c, kpt, precision, Y, HY, ncol, veff64, veff32);
+    subspace_gram(c, precision, cplx, Y, HY, c->Ms, c->Hs, ncol);
+    generalized_eig(c, cplx, c->Ms, c->Hs, eig, ncol);
+    rotate_block(c, precision, cplx, Y, c->Hs, X, ncol);
+}
+
+// Lanczos on one FP64 vector started from the problem's first seeded orbital
+void lanczos(sdft_ctx* c, int spin, int kpt, int steps, double* lower, double* upper) {
+    const bool cplx = c->kb[kpt].cplx;
+    const long long len = c->ng * (cplx ? 2 : 1);
+    double* v = c->work64 + 0 * 2 * c->ng;
+    double* vp = c->work64 + 1 * 2 * c->ng;
+    double* w = c->work64 + 2 * 2 * c->ng;
+    seed_orbitals(c, SDFT_FP64, cplx, v, 1, problem_seed(c, spin, kpt));
+    SDFT_CUDA(cudaMemsetAsync(vp, 0, sizeof(double) * len, c->stream));
+    const double* veff = c->veff + (long long)spin * c->ng;
+    double nrm;
+    {
+        const double* A[1] = {v};
+        dots_host(c, 1, A, A, len, &nrm);
+    }
+    axpby_dev(c, v, v, 1.0 / std::sqrt(nrm), 0.0, len);
+    std::vector<double> al, be;
+    double beta = 0.0;
+    for (int j = 0; j < steps; ++j) {
+        apply_h(c, kpt, SDFT_FP64, v, w, 1, veff, nullptr);
+        double alpha;
+        {
+            const double* A[1] = {v};
+            const double* B[1] = {w};
+            dots_host(c, 1, A, B, len, &alpha);
+        }
+        lincomb_kernel<<<nb(len), 256, 0, c->stream>>>(w, v, vp, 1.0, -alpha, -beta, len);
+        count_launch(c);
+        double bn2;
+        {
+            const double* A[1] = {w};
+            dots_host(c, 1, A, A, len, &bn2);
+        }
+        const double bnext = std::sqrt(bn2);
+        al.push_back(alpha);
+        be.push_back(bnext);
+        // vp = v; v = w / bnext
+        SDFT_CUDA(cudaMemcpyAsync(vp, v, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
+        lincomb_kernel<<<nb(len), 256, 0, c->stream>>>(v, w, nullptr, 0.0, 1.0 / bnext, 0.0, len);
+        count_launch(c);
+        beta = bnext;
+    }
+    std::vector<double> off(be.begin(), be.end() - 1);
+    *lower = tridiag_eig(al, off, 0);
+    *upper = tridiag_eig(al, off, (int)al.size() - 1) + be.back();
+}
+
+void reset_state(sdft_ctx* c) {
+    const long long ng = c->ng;
+    const int ns = c->opt.nspin;
+    if (c->user_density) {
+        SDFT_CUDA(cudaMemcpyAsync(c->rho_in, c->rho_user, sizeof(double) * ns * ng, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        spin_split_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_sad, ns, c->opt.initial_moment, c->rho_in, ng);
+        count_launch(c);
+    }
+    SDFT_CUDA(cudaMemsetAsync(c->phi, 0, sizeof(double) * ng, c->stream));
+    for (Problem& P : c->probs) {
+        seed_orbitals(c, c->opt.precision, P.cplx, P.X, c->opt.nstates, problem_seed(c, P.spin, P.kpt));
+        P.have_bounds = false;
+    }
+    c->mix_k = 0;
+    c->mix_count = 0;
+    c->mix_head = 0;
+    c->log.clear();
+    SDFT_CUDA(cudaGetLastError());
+}
+
+// one CheFSI pass of problem P at the current V_eff in `precision`
+static void chefsi_pass(sdft_ctx* c, Problem& P, int precision, void* X) {
+    const int ns = c->opt.nstates;
+    const double* v64 = c->veff + (long long)P.spin * c->ng;
+    const float* v32 = c->veff32 + (long long)P.spin * c->ng;
+    void* Y = c->blk[0];
+    chebyshev_filter(c, P.kpt, precision, X, Y, ns, c->opt.cheb_degree, P.cutoff, P.upper, P.lower, v64, v32);
+    rayleigh_ritz(c, P.kpt, precision, Y, X, P.eig, ns, v64, v32);
+    double e2[2];
+    SDFT_CUDA(cudaMemcpyAsync(&e2[0], P.eig, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaMemcpyAsync(&e2[1], P.eig + ns - 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    if (!std::isfinite(e2[0]) || !std::isfinite(e2[1])) throw Error{SDFT_ERR_NONFINITE, "Ritz values are not finite"};
+    P.lower = e2[0];
+    P.cutoff = e2[1];
+}
+
+struct Energies {
+    double F, mu, ts, eband;
+};
+
+// Harris-Foulkes free energy from rho_in quantities and the band energy (all on device)
+static Energies energy_hf(sdft_ctx* c, const double* rho_in, const double* veff, const double* exc,
+                          const double* phi, double* rho_tot_tmp) {
+    const int ns = c->opt.nspin;
+    const long long ng = c->ng;
+    double mu_ts_eb[3];
+    SDFT_CUDA(cudaMemcpyAsync(mu_ts_eb, c->scal + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(rho_in, ns, nullptr, rho_tot_tmp, ng);
+    count_launch(c);
+    double* rb = rho_tot_tmp + ng;  // rho_tot + b
+    sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(rho_in, ns, c->b, rb, ng);
+    count_launch(c);
+    const double* A[3] = {veff, exc, rb};
+    const double* B[3] = {rho_in, rho_tot_tmp, phi};
+    double d[3];
+    // veff . rho_in over all spins (nspin*ng contiguous)
+    double vr;
+    {
+        const double* a1[1] = {veff};
+        const double* b1[1] = {rho_in};
+        dots_host(c, 1, a1, b1, ns * ng, &vr);
+    }
+    dots_host(c, 3, A, B, ng, d);
+    Energies E;
+    E.mu = mu_ts_eb[0];
+    E.ts = mu_ts_eb[1];
+    E.eband = mu_ts_eb[2];
+    E.F = E.eband - c->dV * vr + c->dV * d[1] + 0.5 * c->dV * d[2] - c->E_self + c->E_sc + E.ts;
+    return E;
+}
+
+static void density_all(sdft_ctx* c, int precision, bool fp64_copy) {
+    const int ns = c->opt.nstates;
+    SDFT_CUDA(cudaMemsetAsync(c->rho_out, 0, sizeof(double) * c->opt.nspin * c->ng, c->stream));
+    for (Problem& P : c->probs) {
+        const void* X = fp64_copy ? P.X64 : P.X;
+        density_accumulate(c, precision, P.cplx, X, P.occ, ns, c->kw[P.kpt], c->rho_out + (long long)P.spin * c->ng);
+    }
+}
+
+sdft_status run_scf(sdft_ctx* c, sdft_result* out) {
+    const long long ng = c->ng;
+    const int nsp = c->opt.nspin;
+    const long long nv = nsp * ng;
+    c->log.clear();
+    double* ftmp = c->work64 + 20 * ng;   // rho_tot + b
+    double* etmp = c->work64 + 21 * ng;   // two grid vectors for energies
+    double* diff = c->work64 + 18 * ng;   // rho_out - rho_in (2 ng)
+    double t_filter = 0, t_rr = 0, t_pois = 0;
+    const double t0 = now_s();
+    bool converged = false;
+    int it = 0;
+    sdft_status status = SDFT_OK;
+    Energies E{};
+    const int prec = c->opt.precision;
+    for (it = 0; it < c->opt.max_scf; ++it) {
+        // potentials from rho_in (paper Sec. 2.1: Poisson by AAR, then V_eff = phi + V_xc)
+        double ta = now_s();
+        sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_in, nsp, c->b, ftmp, ng);
+        count_launch(c);
+        const int pit = poisson_aar(c, ftmp, c->phi, c->opt.poisson_tol, 2000);
+        if (pit < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Poisson AAR did not converge"};
+        veff_assemble(c);
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+        t_pois += now_s() - ta;
+        // CheFSI for every problem
+        for (Problem& P : c->probs) {
+            if (!P.have_bounds) {
+                double lo, up;
+                lanczos(c, P.spin, P.kpt, c->opt.lanczos_steps, &lo, &up);
+                P.lower = lo;
+                P.upper = up;
+                P.cutoff = lo + 0.1 * (up - lo);
+                P.have_bounds = true;
+            }
+            const int passes = it == 0 ? std::max(1, c->opt.first_scf_filter_passes) : 1;
+            for (int p = 0; p < passes; ++p) {
+                ta = now_s();
+                chefsi_pass(c, P, prec, P.X);
+                t_filter += now_s() - ta;
+            }
+        }
+        // occupations, density, energy, error
+        fermi_device(c, c->probs[0].eig, c->probs[0].occ, c->scal + 8);
+        density_all(c, prec, false);
+        E = energy_hf(c, c->rho_in, c->veff, c->exc, c->phi, etmp);
+        SDFT_CUDA(cudaMemcpyAsync(diff, c->rho_out, sizeof(double) * nv, cudaMemcpyDeviceToDevice, c->stream));
+        axpby_dev(c, diff, c->rho_in, -1.0, 1.0, nv);
+        double nn[2];
+        {
+            const double* A[2] = {diff, c->rho_out};
+            const double* B[2] = {diff, c->rho_out};
+            dots_host(c, 2, A, B, nv, nn);
+        }
+        const double err = std::sqrt(nn[0] / nn[1]);
+        if (!std::isfinite(err) || !std::isfinite(E.F)) throw Error{SDFT_ERR_NONFINITE, "SCF produced non-finite values"};
+        sdft_iter_record rec{};
+        rec.iter = it;
+        rec.energy = E.F;
+        rec.scf_error = err;
+        rec.mu = E.mu;
+        rec.seconds = now_s() - t0;
+        rec.lower = c->probs[0].lower;
+        rec.cutoff = c->probs[0].cutoff;
+        rec.upper = c->probs[0].upper;
+        c->log.push_back(rec);
+        if (err < c->opt.scf_tol) {
+            converged = true;
+            break;
+        }
+        if (it + 1 < c->opt.max_scf) pulay_update(c);
+    }
+    const int niter = std::min(it + 1, c->opt.max_scf);
+    if (!converged) status = SDFT_ERR_NOT_CONVERGED;
+    // final FP64 pass for the mixed path, at the last V_eff
+    bool have64 = prec == SDFT_FP64;
+    if (prec == SDFT_MIXED && c->opt.final_fp64_pass) {
+        for (Problem& P : c->probs) {
+            convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, c->opt.nstates);
+            chefsi_pass(c, P, SDFT_FP64, P.X64);
+        }
+        fermi_device(c, c->probs[0].eig, c->probs[0].occ, c->scal + 8);
+        density_all(c, SDFT_FP64, true);
+        E = energy_hf(c, c->rho_in, c->veff, c->exc, c->phi, etmp);
+        have64 = true;
+    }
+    // Kohn-Sham form at rho_out: phi[rho_out], eps_xc[rho_out]
+    double Fks = 0.0;
+    {
+        double* phi_o = c->work64 + 23 * ng;
+        double* exc_o = c->work64 + 24 * ng;
+        SDFT_CUDA(cudaMemcpyAsync(phi_o, c->phi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, c->stream));
+        sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_out, nsp, c->b, ftmp, ng);
+        count_launch(c);
+        const int pit = poisson_aar(c, ftmp, phi_o, c->opt.poisson_tol, 2000);
+        if (pit < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Poisson AAR did not converge"};
+        double* vxc_o = c->work64 + 25 * ng;  // [nspin][ng]
+        lda_device(c, nsp, c->rho_out, exc_o, vxc_o, (size_t)ng);
+        sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_out, nsp, nullptr, etmp, ng);
+        sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_out, nsp, c->b, etmp + ng, ng);
+        count_launch(c, 2);
+        double vr, d[2];
+        const double* a1[1] = {c->veff};
+        const double* b1[1] = {c->rho_out};
+        dots_host(c, 1, a1, b1, nv, &vr);
+        const double* A[2] = {exc_o, etmp + ng};
+        const double* B[2] = {etmp, phi_o};
+        dots_host(c, 2, A, B, ng, d);
+        Fks = E.eband - c->dV * vr + c->dV * d[0] + 0.5 * c->dV * d[1] - c->E_self + c->E_sc + E.ts;
+    }
+    // results to host
+    const int ns = c->opt.nstates;
+    const size_t ne = c->probs.size() * ns;
+    c->eig_host.resize(ne);
+    c->occ_host.resize(ne);
+    SDFT_CUDA(cudaMemcpyAsync(c->eig_host.data(), c->probs[0].eig, sizeof(double) * ne, cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaMemcpyAsync(c->occ_host.data(), c->probs[0].occ, sizeof(double) * ne, cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    c->mu = E.mu;
+    c->ts = E.ts;
+    if (!have64)
+        for (Problem& P : c->probs) convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, ns);
+    forces_compute(c);
+    if (out) {
+        out->energy = E.F;
+        out->energy_ks = Fks;
+        out->mu = E.mu;
+        out->entropy_term = E.ts;
+        out->niter = niter;
+        out->converged = converged ? 1 : 0;
+        out->t_total = now_s() - t0;
+        out->t_filter = t_filter;
+        out->t_rr = t_rr;
+        out->t_poisson = t_pois;
+        out->t_other = out->t_total - t_filter - t_pois;
+    }
+    return status;
+}
+
+}  // namespace sdft

@@ -1,0 +1,445 @@
+// Matrix-free Hamiltonian application fused with the Chebyshev three-term recurrence
+// (paper Sec. 2.1: "Hamiltonian-matrix/vector products are performed in matrix-free fashion,
+// using the finite-difference stencil for the Laplacian and the outer product nature of the
+// nonlocal pseudopotential operator"; filter of Zhou et al. 2006 / Zhou & Saad 2007).
+//
+//   Ynext = alpha * (H Y - shift * Y) - beta * Yprev,
+//   H Y   = -1/2 L_h Y + V .* Y + sum_a beta_a (gamma_a beta_a^H Y)
+//
+// Kernel design (GB300): one CTA owns a TX x TY column tile of the grid and marches along z
+// for one element-column.  The 13 z-neighbours of each thread's point live in a register
+// queue (plus PF planes of prefetch), so every Y value enters the SM once from its own
+// column; only the x/y halo of the current plane goes through shared memory (double-buffered,
+// one __syncthreads per plane).  Periodic/Bloch wrap is done with index arithmetic on the
+// loads (TMA's zero fill cannot express a periodic halo).  FP32 blocks carry two lanes per
+// element (two orbitals, or re/im) and use Blackwell's packed f32x2 FMA.
+#pragma once
+#include <type_traits>
+#include "internal.cuh"
+
+namespace sdft {
+namespace {
+
+// ---- element arithmetic ---------------------------------------------------------------
+__device__ __forceinline__ unsigned long long f2u(float2 a) {
+    return (unsigned long long)__float_as_uint(a.x) | ((unsigned long long)__float_as_uint(a.y) << 32);
+}
+__device__ __forceinline__ float2 u2f(unsigned long long u) {
+    return make_float2(__uint_as_float((unsigned)(u & 0xffffffffu)), __uint_as_float((unsigned)(u >> 32)));
+}
+// acc + s * a   (scalar s broadcast to both lanes)
+__device__ __forceinline__ float2 efma(float s, float2 a, float2 acc) {
+    unsigned long long r;
+    unsigned long long ss = f2u(make_float2(s, s));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(ss), "l"(f2u(a)), "l"(f2u(acc)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 eadd(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+// lane-wise a * b + acc
+__device__ __forceinline__ float2 efma2(float2 a, float2 b, float2 acc) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(acc)));
+    return u2f(r);
+}
+__device__ __forceinline__ double efma(double s, double a, double acc) { return fma(s, a, acc); }
+__device__ __forceinline__ double eadd(double a, double b) { return a + b; }
+__device__ __forceinline__ double efma2(double a, double b, double acc) { return fma(a, b, acc); }
+__device__ __forceinline__ double2 efma(double s, double2 a, double2 acc) {
+    return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y));
+}
+__device__ __forceinline__ double2 eadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 efma2(double2 a, double2 b, double2 acc) {
+    return make_double2(fma(a.x, b.x, acc.x), fma(a.y, b.y, acc.y));
+}
+
+template <typename E> __device__ __forceinline__ E ezero();
+template <> __device__ __forceinline__ float2 ezero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double ezero<double>() { return 0.0; }
+template <> __device__ __forceinline__ double2 ezero<double2>() { return make_double2(0.0, 0.0); }
+
+// complex multiply (for CPLX element types): a * b
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // conj(a) * b
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+template <typename S>
+struct StepArgs {
+    S cx[FD_RADIUS + 1], cy[FD_RADIUS + 1], cz[FD_RADIUS + 1];
+    S c0, alpha, beta, shift;
+    S phr[3], phi[3];           // Bloch phase exp(2 pi i kappa_d) per axis
+    int n1, n2, n3, zchunk, nzc, natom;
+    long long ng;
+};
+
+__device__ __forceinline__ int wrapi(int x, int n, int& t) {
+    // x in any range -> [0, n), t = floor(x / n)
+    int q = x / n;
+    int r = x - q * n;
+    if (r < 0) { r += n; --q; }
+    t = q;
+    return r;
+}
+
+template <typename E, typename S>
+__device__ __forceinline__ E apply_phase(E v, int t, S pr, S pi) {
+    return v;
+}
+template <>
+__device__ __forceinline__ float2 apply_phase<float2, float>(float2 v, int t, float pr, float pi) {
+    // v * (pr + i pi)^t, t small
+    float2 w = v;
+    if (t > 0) {
+        for (int k = 0; k < t; ++k) w = cmul(w, make_float2(pr, pi));
+    } else {
+        for (int k = 0; k < -t; ++k) w = cmul(w, make_float2(pr, -pi));
+    }
+    return w;
+}
+template <>
+__device__ __forceinline__ double2 apply_phase<double2, double>(double2 v, int t, double pr, double pi) {
+    double2 w = v;
+    if (t > 0) {
+        for (int k = 0; k < t; ++k) w = cmul(w, make_double2(pr, pi));
+    } else {
+        for (int k = 0; k < -t; ++k) w = cmul(w, make_double2(pr, -pi));
+    }
+    return w;
+}
+
+// Column of a load: flat xy offset of the wrapped (x, y) and its Bloch phase (complex blocks).
+template <typename E>
+struct ColRef {
+    long long base;
+    E ph;
+};
+
+template <typename E> __device__ __forceinline__ E eone();
+template <> __device__ __forceinline__ float2 eone<float2>() { return make_float2(1.f, 0.f); }
+template <> __device__ __forceinline__ double eone<double>() { return 1.0; }
+template <> __device__ __forceinline__ double2 eone<double2>() { return make_double2(1.0, 0.0); }
+
+template <typename E, typename S, bool CPLX>
+__device__ __forceinline__ ColRef<E> make_col(int x, int y, const StepArgs<S>& A) {
+    int tx, ty;
+    int wx = wrapi(x, A.n1, tx), wy = wrapi(y, A.n2, ty);
+    ColRef<E> r;
+    r.base = (long long)wy * A.n1 + wx;
+    r.ph = eone<E>();
+    if constexpr (CPLX) {
+        if (tx) r.ph = apply_phase<E, S>(r.ph, tx, A.phr[0], A.phi[0]);
+        if (ty) r.ph = apply_phase<E, S>(r.ph, ty, A.phr[1], A.phi[1]);
+    }
+    return r;
+}
+
+// load the element of column `cr` at unwrapped plane z (Bloch phases for complex blocks)
+template <typename E, typename S, bool CPLX>
+__device__ __forceinline__ E load_col(const E* __restrict__ Yc, const ColRef<E>& cr, int z,
+                                      const StepArgs<S>& A) {
+    int tz;
+    const int wz = wrapi(z, A.n3, tz);
+    E v = Yc[(long long)wz * A.n1 * A.n2 + cr.base];
+    if constexpr (CPLX) {
+        if constexpr (Elem<E>::lanes == 2 && !std::is_same<E, double>::value) {
+            v = cmul(v, cr.ph);
+            if (tz) v = apply_phase<E, S>(v, tz, A.phr[2], A.phi[2]);
+        }
+    }
+    return v;
+}
+
+// KB scatter value at point g for element-column col
+template <typename E, typename S, bool CPLX>
+__device__ __forceinline__ E kb_term(long long g, int col, const int* __restrict__ pcnt,
+                                     const int* __restrict__ patom, const void* __restrict__ pval,
+                                     const E* __restrict__ C, long long ng, int natom) {
+    E acc = ezero<E>();
+    int cnt = __ldg(pcnt + g);
+    for (int s = 0; s < cnt; ++s) {
+        int a = __ldg(patom + s * ng + g);
+        E cv = C[(long long)col * natom + a];
+        if constexpr (CPLX) {
+            E bv = reinterpret_cast<const E*>(pval)[s * ng + g];
+            acc = eadd(acc, cmul(bv, cv));
+        } else {
+            S bv = reinterpret_cast<const S*>(pval)[s * ng + g];
+            acc = efma(bv, cv, acc);
+        }
+    }
+    return acc;
+}
+
+template <typename E, bool CPLX, int TX, int TY, int PF, bool PREV, bool KB, bool VLOC, bool KIN>
+__global__ void __launch_bounds__(TX * TY)
+cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __restrict__ Ynext,
+                 const typename Elem<E>::S* __restrict__ V, const E* __restrict__ C,
+                 const int* __restrict__ pcnt, const int* __restrict__ patom,
+                 const void* __restrict__ pval, const StepArgs<typename Elem<E>::S> A) {
+    using S = typename Elem<E>::S;
+    constexpr int R = FD_RADIUS;
+    constexpr int QN = 2 * R + 1 + PF;      // register queue length
+    constexpr int HW = TX + 2 * R;          // smem tile width
+    constexpr int HH = TY + 2 * R;
+    constexpr int NT = TX * TY;
+    constexpr int NHALO = 2 * R * (TX + TY);
+    constexpr int HPT = (NHALO + NT - 1) / NT;  // halo elements per thread
+    __shared__ E tile[2][HH][HW];
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * TX + tx;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int col = blockIdx.z / A.nzc;
+    const int zc = blockIdx.z - col * A.nzc;
+    const int z0 = zc * A.zchunk;
+    const int z1 = min(A.n3, z0 + A.zchunk);
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool valid = gx < A.n1 && gy < A.n2;
+    const E* __restrict__ Yc = Y + (long long)col * A.ng;
+
+    // halo slots owned by this thread: local (ly, lx) in the tile
+    int hly[HPT], hlx[HPT];
+    ColRef<E> hcol[HPT];
+#pragma unroll
+    for (int k = 0; k < HPT; ++k) {
+        int i = tid + k * NT;
+        if (i < 2 * R * TY) {               // x halo: rows 0..TY-1, 6 columns left and right
+            int row = i / (2 * R), j = i - row * (2 * R);
+            hly[k] = R + row;
+            hlx[k] = j < R ? j : TX + j;
+        } else if (i < NHALO) {             // y halo: 6 rows above and below, TX columns
+            int j = i - 2 * R * TY;
+            int row = j / TX, cc = j - row * TX;
+            hly[k] = row < R ? row : TY + row;
+            hlx[k] = R + cc;
+        } else {
+            hly[k] = -1;
+            hlx[k] = 0;
+        }
+        hcol[k] = make_col<E, S, CPLX>(x0 - R + hlx[k], y0 - R + max(hly[k], 0), A);
+    }
+    const ColRef<E> mycol = make_col<E, S, CPLX>(gx, gy, A);
+
+    E q[QN];
+    // prologue: planes z0-6 .. z0+5+PF  (queue slot s holds plane z0 - 6 + s + QN*m)
+#pragma unroll
+    for (int s = 0; s < 2 * R + PF; ++s)
+        q[s] = load_col<E, S, CPLX>(Yc, mycol, z0 - R + s, A);
+    E hreg[HPT];
+#pragma unroll
+    for (int k = 0; k < HPT; ++k)
+        if (hly[k] >= 0) hreg[k] = load_col<E, S, CPLX>(Yc, hcol[k], z0, A);
+
+    for (int zb = z0; zb < z1; zb += QN) {
+#pragma unroll
+        for (int ph = 0; ph < QN; ++ph) {
+            const int z = zb + ph;
+            if (z < z1) {
+                E (*T)[HW] = tile[(z - z0) & 1];
+                // slot of plane z + dz is (ph + R + dz) mod QN
+                const E center = q[(ph + R) % QN];
+                T[R + ty][R + tx] = center;
+#pragma unroll
+                for (int k = 0; k < HPT; ++k)
+                    if (hly[k] >= 0) T[hly[k]][hlx[k]] = hreg[k];
+                // prefetch plane z + R + PF into the slot of plane z - R - 1
+                q[(ph + 2 * R + PF) % QN] = load_col<E, S, CPLX>(Yc, mycol, z + R + PF, A);
+                if (z + 1 < z1) {
+#pragma unroll
+                    for (int k = 0; k < HPT; ++k)
+                        if (hly[k] >= 0)
+                            hreg[k] = load_col<E, S, CPLX>(Yc, hcol[k], z + 1, A);
+                }
+                const long long g = ((long long)z * A.n2 + gy) * A.n1 + gx;
+                E prev = ezero<E>();
+                S vloc = S(0);
+                if (valid) {
+                    if (PREV) prev = Yprev[(long long)col * A.ng + g];
+                    if (VLOC) vloc = V[g];
+                }
+                __syncthreads();
+                if (valid) {
+                    E acc = ezero<E>();
+                    if (KIN) {
+                        acc = efma(A.c0, center, acc);
+#pragma unroll
+                        for (int r = 1; r <= R; ++r) {
+                            acc = efma(A.cz[r], eadd(q[(ph + R + r) % QN], q[(ph + R - r + QN) % QN]), acc);
+                            acc = efma(A.cx[r], eadd(T[R + ty][R + tx + r], T[R + ty][R + tx - r]), acc);
+                            acc = efma(A.cy[r], eadd(T[R + ty + r][R + tx], T[R + ty - r][R + tx]), acc);
+                        }
+                    }
+                    if (VLOC) acc = efma(vloc, center, acc);
+                    if (KB) acc = eadd(acc, kb_term<E, S, CPLX>(g, col, pcnt, patom, pval, C, A.ng, A.natom));
+                    // out = alpha * (acc - shift * center) - beta * prev
+                    E t = efma(-A.shift, center, acc);
+                    E out = ezero<E>();
+                    out = efma(A.alpha, t, out);
+                    if (PREV) out = efma(-A.beta, prev, out);
+                    Ynext[(long long)col * A.ng + g] = out;
+                }
+            }
+        }
+    }
+}
+
+// KB projection: C[col][a] = gamma_a * sum_j conj(beta_a(j)) Y[idx_j, col], NC columns per CTA
+template <typename E, bool CPLX, int NC>
+__global__ void __launch_bounds__(256)
+kb_project_kernel(const E* __restrict__ Y, E* __restrict__ C, const int* __restrict__ cnt,
+                  const int* __restrict__ idx, const void* __restrict__ val,
+                  const double* __restrict__ gamma, int cap, int natom, int ncolE, long long ng) {
+    using S = typename Elem<E>::S;
+    const int a = blockIdx.x;
+    const int c0 = blockIdx.y * NC;
+    const int m = cnt[a];
+    E acc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k] = ezero<E>();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        const long long e = (long long)a * cap + j;
+        const int g = idx[e];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            if (c0 + k < ncolE) {
+                E y = Y[(long long)(c0 + k) * ng + g];
+                if constexpr (CPLX) {
+                    E b = reinterpret_cast<const E*>(val)[e];
+                    acc[k] = eadd(acc[k], cmul_conj(b, y));
+                } else {
+                    S b = reinterpret_cast<const S*>(val)[e];
+                    acc[k] = efma(b, y, acc[k]);
+                }
+            }
+        }
+    }
+    // block reduction (warp shuffles, then smem across warps)
+    __shared__ E red[NC][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        E v = acc[k];
+        for (int off = 16; off > 0; off >>= 1) {
+            if constexpr (sizeof(E) == 8 && Elem<E>::lanes == 1) {
+                v += __shfl_down_sync(0xffffffffu, v, off);
+            } else {
+                E o;
+                o.x = __shfl_down_sync(0xffffffffu, v.x, off);
+                o.y = __shfl_down_sync(0xffffffffu, v.y, off);
+                v = eadd(v, o);
+            }
+        }
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NC && c0 + (int)threadIdx.x < ncolE) {
+        const int k = threadIdx.x;
+        E v = red[k][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = eadd(v, red[k][w]);
+        const S gm = (S)gamma[a];
+        E out = efma(gm, v, ezero<E>());
+        C[(long long)(c0 + k) * natom + a] = out;
+    }
+}
+
+template <typename S>
+StepArgs<S> make_args(sdft_ctx* c, int kpt, double alpha, double beta, double shift, int zchunk, int nzc) {
+    StepArgs<S> A;
+    for (int r = 0; r <= FD_RADIUS; ++r) {
+        A.cx[r] = (S)c->coef.cx[r];
+        A.cy[r] = (S)c->coef.cy[r];
+        A.cz[r] = (S)c->coef.cz[r];
+    }
+    A.c0 = (S)c->coef.c0;
+    A.alpha = (S)alpha;
+    A.beta = (S)beta;
+    A.shift = (S)shift;
+    for (int d = 0; d < 3; ++d) {
+        double kd = c->kpts.empty() ? 0.0 : c->kpts[3 * kpt + d];
+        A.phr[d] = (S)cos(2.0 * M_PI * kd);
+        A.phi[d] = (S)sin(2.0 * M_PI * kd);
+    }
+    A.n1 = c->n[0];
+    A.n2 = c->n[1];
+    A.n3 = c->n[2];
+    A.zchunk = zchunk;
+    A.nzc = nzc;
+    A.natom = c->natom;
+    A.ng = c->ng;
+    return A;
+}
+
+template <typename E, bool CPLX, int TX, int TY, int PF>
+void launch_variant(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, int ncolE,
+                    const typename Elem<E>::S* V, const E* kbC, double alpha, double beta, double shift,
+                    bool kin) {
+    using S = typename Elem<E>::S;
+    const int tiles = ((c->n[0] + TX - 1) / TX) * ((c->n[1] + TY - 1) / TY);
+    // enough CTAs to fill 152 SMs several times over; each z chunk >= 16 planes
+    long long want = 8LL * 152;
+    int nzc = 1;
+    while ((long long)tiles * ncolE * nzc < want && c->n[2] / (nzc + 1) >= 16) ++nzc;
+    const int zchunk = (c->n[2] + nzc - 1) / nzc;
+    nzc = (c->n[2] + zchunk - 1) / zchunk;
+    StepArgs<S> A = make_args<S>(c, kpt, alpha, beta, shift, zchunk, nzc);
+    dim3 grid((c->n[0] + TX - 1) / TX, (c->n[1] + TY - 1) / TY, (unsigned)(ncolE * nzc));
+    dim3 block(TX, TY);
+    const KBTables& kb = c->kb[kpt];
+    const void* pval = std::is_same<S, float>::value ? (const void*)kb.pval32 : (const void*)kb.pval64;
+    const bool prev = Yprev != nullptr, hasv = V != nullptr, haskb = kbC != nullptr && kb.S > 0;
+#define SDFT_STEP(P, K, VV, KN)                                                                      \
+    cheb_step_kernel<E, CPLX, TX, TY, PF, P, K, VV, KN><<<grid, block, 0, c->stream>>>(               \
+        Y, Yprev, Ynext, V, kbC, kb.pcnt, kb.patom, pval, A)
+    SDFT_REQUIRE(kin, SDFT_ERR_INVALID_ARG, "stencil step without kinetic term is not built");
+    if (hasv) {
+        if (prev && haskb) SDFT_STEP(true, true, true, true);
+        else if (!prev && haskb) SDFT_STEP(false, true, true, true);
+        else if (prev && !haskb) SDFT_STEP(true, false, true, true);
+        else SDFT_STEP(false, false, true, true);
+    } else {
+        // Laplacian-only form used by the Poisson solver (FP64 real, single vector)
+        SDFT_REQUIRE(prev && !haskb, SDFT_ERR_INVALID_ARG, "stencil variant without V_eff needs Yprev and no KB");
+        if constexpr (std::is_same<E, double>::value) SDFT_STEP(true, false, false, true);
+        else SDFT_REQUIRE(false, SDFT_ERR_INVALID_ARG, "Laplacian-only stencil is FP64 real only");
+    }
+#undef SDFT_STEP
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+
+}  // namespace
+
+template <typename E>
+void launch_project_impl(sdft_ctx* c, int kpt, const E* Y, E* C, int ncolE) {
+    const KBTables& kb = c->kb[kpt];
+    if (kb.natom == 0 || ncolE == 0) return;
+    constexpr int NC = 4;
+    dim3 grid(kb.natom, (ncolE + NC - 1) / NC);
+    using S = typename Elem<E>::S;
+    const void* val = std::is_same<S, float>::value ? (const void*)kb.val32 : (const void*)kb.val64;
+    if (kb.cplx) {
+        if constexpr (!std::is_same<E, double>::value)
+            kb_project_kernel<E, true, NC><<<grid, 256, 0, c->stream>>>(Y, C, kb.cnt, kb.idx, val, kb.gamma,
+                                                                       kb.cap, kb.natom, ncolE, c->ng);
+    } else {
+        kb_project_kernel<E, false, NC><<<grid, 256, 0, c->stream>>>(Y, C, kb.cnt, kb.idx, val, kb.gamma, kb.cap,
+                                                                    kb.natom, ncolE, c->ng);
+    }
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+}  // namespace sdft

@@ -1,0 +1,226 @@
+"""GPU parity of each hot-path step against the FP64 CPU oracle, elementwise, through the C ABI.
+
+Tolerances: FP64 kernels agree with the oracle to round-off (1e-12 relative for one H X,
+growing linearly with the number of recurrence steps).  FP32 (SDFT_MIXED) kernels: one H X
+has relative error ~ (37 terms) * 2^-24 * |stencil sum| / |H X| -> 2e-5 of max|H X| is used;
+the degree-m filter accumulates ~m such errors -> 3e-5 * m relative to max|Y|.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import workloads  # noqa: E402
+from oracle import chefsi, ham, model, xc  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def sd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_10431_gb300 import build
+    build.build()
+    import paper_2005_10431_gb300 as m
+    return m
+
+
+def _ctx(sd, cell, precision, nstates, kpts=None, nspin=1):
+    return sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species,
+                          dict(nstates=nstates, precision=precision, nspin=nspin), kpts=kpts)
+
+
+def _ragged_cell():
+    # 9 x 10 x 11 grid (ragged against the 32 x 8 stencil tile), orthorhombic, 3 atoms
+    c = workloads.small_cell(npts=10, L=4.0, natom=3, seed=21, nstates=6)
+    c.n = (9, 10, 11)
+    c.L = (3.6, 4.0, 4.4)
+    return c
+
+
+def _relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def test_setup_fields_match_oracle(sd):
+    for cell in (workloads.two_atom_cell(), _ragged_cell()):
+        ctx = _ctx(sd, cell, sd.SDFT_FP64, 6)
+        b = sd.sdft_get_pseudocharge(ctx)
+        sad = sd.sdft_get_sad_density(ctx)
+        assert _relerr(b, model.pseudocharge(cell)) < 1e-12
+        assert _relerr(sad, model.sad_density(cell)) < 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("kred", [(0.0, 0.0, 0.0), (0.25, -0.375, 0.5)])
+def test_apply_h_matches_oracle(sd, precision, kred):
+    cell = _ragged_cell()
+    cplx = any(kred)
+    ns = 6
+    ctx = _ctx(sd, cell, precision, ns, kpts=[kred] if cplx else None)
+    V = np.random.default_rng(1).normal(0, 0.4, cell.ngrid)
+    sd.sdft_set_veff(ctx, 0, V)
+    X = workloads.initial_orbitals(3, cell.ngrid, ns, complex_valued=cplx)
+    x = sd.pack_block(X, precision)
+    y = torch.empty_like(x)
+    sd.sdft_apply_h(ctx, 0, 0, precision, x, y, ns)
+    P = model.projectors(cell, kred)
+    ref = ham.apply_h(cell, X, V, P, model.kb_energies(cell), kred)
+    got = sd.unpack_block(y, precision, cplx)
+    tol = 1e-12 if precision == sd.SDFT_FP64 else 2e-5
+    assert _relerr(got, ref) < tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_chebyshev_filter_matches_oracle(sd, precision):
+    cell = _ragged_cell()
+    ns, m = 6, 10
+    ctx = _ctx(sd, cell, precision, ns)
+    V = np.random.default_rng(2).normal(0, 0.4, cell.ngrid)
+    sd.sdft_set_veff(ctx, 0, V)
+    X = workloads.initial_orbitals(4, cell.ngrid, ns)
+    a, b, a0 = 3.0, 90.0, -1.5
+    x = sd.pack_block(X, precision)
+    y = torch.empty_like(x)
+    sd.sdft_chebyshev_filter(ctx, 0, 0, precision, x, y, ns, m, a, b, a0)
+    P = model.projectors(cell)
+    ref = chefsi.chebyshev_filter(lambda Z: ham.apply_h(cell, Z, V, P, model.kb_energies(cell)), X, m, a, b, a0)
+    tol = 1e-11 if precision == sd.SDFT_FP64 else 3e-5 * m
+    assert _relerr(sd.unpack_block(y, precision, False), ref) < tol
+
+
+@pytest.mark.parametrize("kred", [(0.0, 0.0, 0.0), (0.5, 0.25, 0.0)])
+def test_rayleigh_ritz_fp64_matches_oracle(sd, kred):
+    cell = _ragged_cell()
+    cplx = any(kred)
+    ns = 6
+    ctx = _ctx(sd, cell, sd.SDFT_FP64, ns, kpts=[kred] if cplx else None)
+    V = np.random.default_rng(3).normal(0, 0.4, cell.ngrid)
+    sd.sdft_set_veff(ctx, 0, V)
+    P = model.projectors(cell, kred)
+    apply = lambda Z: ham.apply_h(cell, Z, V, P, model.kb_energies(cell), kred)
+    Y = chefsi.chebyshev_filter(apply, workloads.initial_orbitals(6, cell.ngrid, ns, cplx), 8, 5.0, 80.0, -2.0)
+    lam_ref, X_ref = chefsi.rayleigh_ritz(apply, Y)
+    y = sd.pack_block(Y, sd.SDFT_FP64)
+    x = torch.empty_like(y)
+    eig = torch.empty(ns, dtype=torch.float64, device="cuda")
+    sd.sdft_rayleigh_ritz(ctx, 0, 0, sd.SDFT_FP64, y, x, eig, ns)
+    assert np.allclose(eig.cpu().numpy(), lam_ref, rtol=0, atol=1e-10 * np.max(np.abs(lam_ref)))
+    X = sd.unpack_block(x, sd.SDFT_FP64, cplx)
+    # eigenvectors are unique up to a phase per (non-degenerate) column: compare projectors
+    for n in range(ns):
+        ov = abs(np.vdot(X_ref[n], X[n]))
+        assert abs(ov - 1.0) < 1e-9
+
+
+def test_subspace_matrices_and_rotation_mixed(sd):
+    cell = _ragged_cell()
+    ns = 6
+    ctx = _ctx(sd, cell, sd.SDFT_MIXED, ns)
+    rng = np.random.default_rng(7)
+    Y = rng.normal(size=(ns, cell.ngrid))
+    HY = rng.normal(size=(ns, cell.ngrid))
+    Y32 = Y.astype(np.float32).astype(np.float64)
+    HY32 = HY.astype(np.float32).astype(np.float64)
+    m = torch.empty(ns, ns, dtype=torch.float64, device="cuda")
+    h = torch.empty_like(m)
+    sd.sdft_subspace_matrices(ctx, 0, sd.SDFT_MIXED, sd.pack_block(Y, 1), sd.pack_block(HY, 1), m, h, ns)
+    M_ref = Y32 @ Y32.T
+    H_ref = Y32 @ HY32.T
+    H_ref = 0.5 * (H_ref + H_ref.T)
+    scale = np.sqrt(np.outer(np.diag(M_ref), np.diag(M_ref)))
+    # column-major result: element (i, j) at i + j*ns -> tensor [j, i]
+    assert np.max(np.abs(m.cpu().numpy().T - M_ref) / scale) < 1e-5
+    Hs = h.cpu().numpy().T
+    # the library mirrors the upper triangle of Y^T HY
+    upper = np.triu(Y32 @ HY32.T)
+    H_lib_ref = upper + np.triu(upper, 1).T
+    assert np.max(np.abs(Hs - H_lib_ref) / scale) < 1e-5
+    Q = rng.normal(size=(ns, ns))
+    q = torch.from_numpy(np.ascontiguousarray(Q.T)).cuda()   # column-major Q
+    x = torch.empty_like(sd.pack_block(Y, 1))
+    sd.sdft_rotate(ctx, 0, sd.SDFT_MIXED, sd.pack_block(Y, 1), q, x, ns)
+    ref = (Y32.T @ Q.astype(np.float32).astype(np.float64)).T
+    assert _relerr(sd.unpack_block(x, 1, False), ref) < 1e-5
+
+
+def test_poisson_aar_matches_exact_solve(sd):
+    cell = workloads.two_atom_cell()
+    ctx = _ctx(sd, cell, sd.SDFT_FP64, 8)
+    f = model.sad_density(cell) + model.pseudocharge(cell)
+    ref = ham.poisson_exact(cell, f)
+    ft = torch.from_numpy(f).cuda()
+    phi = torch.zeros_like(ft)
+    it = sd.sdft_poisson(ctx, ft, phi, 1e-12, 3000)
+    assert it > 0
+    assert _relerr(phi.cpu().numpy(), ref) < 1e-9
+
+
+@pytest.mark.parametrize("nspin", [1, 2])
+def test_lda_matches_oracle(sd, nspin):
+    cell = workloads.two_atom_cell()
+    ctx = _ctx(sd, cell, sd.SDFT_FP64, 8)
+    rng = np.random.default_rng(4)
+    n = 5000
+    rho = 10 ** rng.uniform(-6, 1.5, (nspin, n))
+    exc = torch.empty(n, dtype=torch.float64, device="cuda")
+    vxc = torch.empty(nspin * n, dtype=torch.float64, device="cuda")
+    sd.sdft_lda(ctx, nspin, torch.from_numpy(rho.reshape(-1)).cuda(), exc, vxc, n)
+    if nspin == 1:
+        e_ref, v_ref = xc.lda_pz_unpolarized(rho[0])
+        v_ref = v_ref[None]
+    else:
+        e_ref, vu, vd = xc.lda_pz_polarized(rho[0], rho[1])
+        v_ref = np.stack([vu, vd])
+    assert np.max(np.abs(exc.cpu().numpy() - e_ref) / np.abs(e_ref)) < 1e-13
+    assert np.max(np.abs(vxc.cpu().numpy().reshape(nspin, n) - v_ref) / np.abs(v_ref)) < 1e-13
+
+
+def test_fermi_matches_oracle(sd):
+    cell = workloads.two_atom_cell()
+    ctx = _ctx(sd, cell, sd.SDFT_FP64, 8)
+    eigs = np.sort(np.random.default_rng(5).normal(0, 0.3, (1, 1, 8)), axis=-1)
+    e = torch.from_numpy(eigs.reshape(-1)).cuda()
+    occ = torch.empty_like(e)
+    mu, ts = sd.sdft_fermi(ctx, e, occ)
+    mu_ref, g_ref = ham.fermi_occupations(eigs, np.ones(1), cell.nelec, cell.kT, 2.0)
+    assert abs(mu - mu_ref) < 1e-12
+    assert np.max(np.abs(occ.cpu().numpy() - g_ref.reshape(-1))) < 1e-12
+    assert abs(ts - ham.entropy_term(g_ref, np.ones(1), cell.kT, 2.0)) < 1e-13
+
+
+def test_lanczos_bounds_match_oracle(sd):
+    cell = workloads.two_atom_cell()
+    ctx = _ctx(sd, cell, sd.SDFT_FP64, 8)
+    V = model.sad_density(cell) * 0.1 - 0.5
+    sd.sdft_set_veff(ctx, 0, V)
+    lo, up = sd.sdft_lanczos_bounds(ctx, 0, 0, 20)
+    P = model.projectors(cell)
+    v0 = workloads.initial_orbitals(0 * 4099, cell.ngrid, 1)[0]
+    lo_r, up_r = chefsi.lanczos_bounds(lambda Z: ham.apply_h(cell, Z, V, P, model.kb_energies(cell)), v0, 20)
+    assert abs(lo - lo_r) < 1e-8 and abs(up - up_r) < 1e-8
+
+
+def test_invalid_arguments_are_rejected(sd):
+    cell = workloads.two_atom_cell()
+    pos = cell.pos.copy()
+    pos[0, 0] = np.nan
+    with pytest.raises(sd.SdftError) as e:
+        sd.sdft_create(cell.L, cell.n, pos, cell.types, cell.species, dict(nstates=8))
+    assert e.value.code == -7
+    with pytest.raises(sd.SdftError) as e:
+        sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species, dict(nstates=7, precision=1))
+    assert e.value.code == -1
+    ctx = _ctx(sd, cell, sd.SDFT_FP64, 8)
+    with pytest.raises(sd.SdftError):
+        sd.sdft_get_eigenvalues(ctx)          # no SCF yet
+    bad = np.full(cell.ngrid, np.inf)
+    with pytest.raises(sd.SdftError) as e:
+        sd.sdft_set_veff(ctx, 0, bad)
+    assert e.value.code == -7

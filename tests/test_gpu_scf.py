@@ -1,0 +1,116 @@
+"""End-to-end SCF parity on the GPU against the FP64 CPU oracle.
+
+FP64 path: converged free energy within 1e-9 Ha/atom and occupied eigenvalues within 1e-8 Ha
+of the oracle (both sides converged to an SCF error of 1e-10).  Mixed path (FP32 filter): within
+1e-5 Ha/atom, 1e-5 Ha eigenvalues and 1e-4 Ha/bohr forces.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import workloads  # noqa: E402
+from oracle import scf as oscf  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def sd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_10431_gb300 import build
+    build.build()
+    import paper_2005_10431_gb300 as m
+    return m
+
+
+def _run(sd, cell, precision, tol, final=0, max_scf=300, kpts=None, kw=None):
+    ctx = sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species,
+                         dict(nstates=cell.nstates, cheb_degree=cell.cheb_degree, precision=precision,
+                              scf_tol=tol, max_scf=max_scf, final_fp64_pass=final, nspin=cell.nspin,
+                              kT=cell.kT, seed=cell.seed),
+                         kpts=kpts, kw=kw)
+    r = sd.sdft_scf(ctx)
+    return ctx, r
+
+
+def _gold(name):
+    return json.load(open(os.path.join(HERE, "golden", name + ".json")))
+
+
+def test_fp64_scf_two_atom_matches_oracle(sd):
+    cell = workloads.two_atom_cell()
+    g = _gold("two_atom_24")
+    ctx, r = _run(sd, cell, sd.SDFT_FP64, 1e-10)
+    assert r["converged"]
+    assert abs(r["energy"] - g["energy"]) / cell.natom < 1e-9
+    assert abs(r["energy_ks"] - g["energy_ks"]) / cell.natom < 1e-9
+    eig = sd.sdft_get_eigenvalues(ctx)[0, 0]
+    occ = np.array(g["occ"])[0, 0]
+    nocc = int(np.sum(occ > 1e-10))
+    assert np.max(np.abs(eig[:nocc] - np.array(g["eigs"])[0, 0, :nocc])) < 1e-8
+    f = sd.sdft_get_forces(ctx)
+    assert np.max(np.abs(f - np.array(g["forces"]))) < 1e-6
+    rho = sd.sdft_get_density(ctx)
+    dV = float(np.prod(cell.h))
+    assert abs(dV * rho.sum() - cell.nelec) < 1e-9
+    log = sd.sdft_get_scf_log(ctx)
+    assert len(log) == r["niter"] and log[-1]["scf_error"] < 1e-10
+
+
+def test_mixed_scf_two_atom_matches_oracle(sd):
+    cell = workloads.two_atom_cell()
+    g = _gold("two_atom_24")
+    ctx, r = _run(sd, cell, sd.SDFT_MIXED, 1e-7, final=1)
+    assert r["converged"]
+    assert abs(r["energy"] - g["energy"]) / cell.natom < 1e-5
+    eig = sd.sdft_get_eigenvalues(ctx)[0, 0]
+    occ = np.array(g["occ"])[0, 0]
+    nocc = int(np.sum(occ > 1e-10))
+    assert np.max(np.abs(eig[:nocc] - np.array(g["eigs"])[0, 0, :nocc])) < 1e-5
+    assert np.max(np.abs(sd.sdft_get_forces(ctx) - np.array(g["forces"]))) < 1e-4
+
+
+def _displaced_small():
+    c = workloads.small_cell(npts=12, L=4.5, natom=2, nstates=6, degree=12)
+    c.pos = np.array([[0.3, 0.2, 0.1], [2.4, 2.1, 2.6]])
+    return c
+
+
+def test_fp64_forces_match_oracle_on_displaced_cell(sd):
+    cell = _displaced_small()
+    ref = oscf.scf(_displaced_small(), tol=1e-10, max_iter=300, with_forces=True)
+    ctx, r = _run(sd, cell, sd.SDFT_FP64, 1e-10)
+    assert abs(r["energy"] - ref.energy) / cell.natom < 1e-9
+    f = sd.sdft_get_forces(ctx)
+    assert np.max(np.abs(f)) > 1e-3
+    assert np.max(np.abs(f - ref.forces)) < 1e-7
+
+
+def test_fp64_spin_kpoint_scf_matches_oracle(sd):
+    # spin-polarised, two k-points (one complex), on a small cell
+    cell = _displaced_small()
+    cell.nspin = 2
+    cell.kpts = np.array([[0.0, 0.0, 0.0], [0.25, 0.0, -0.25]])
+    cell.kw = np.array([0.5, 0.5])
+    ref = oscf.scf(cell, tol=1e-10, max_iter=300)
+    ctx, r = _run(sd, cell, sd.SDFT_FP64, 1e-10, kpts=cell.kpts, kw=cell.kw)
+    assert r["converged"]
+    assert abs(r["energy"] - ref.energy) / cell.natom < 1e-9
+    eig = sd.sdft_get_eigenvalues(ctx)
+    nocc = 4
+    assert np.max(np.abs(eig[:, :, :nocc] - ref.eigs[:, :, :nocc])) < 1e-8
+
+
+def test_not_converged_status_returns_partial_result(sd):
+    cell = workloads.two_atom_cell()
+    ctx, r = _run(sd, cell, sd.SDFT_FP64, 1e-12, max_scf=3)
+    assert r["status"] == -4 and r["niter"] == 3 and not r["converged"]
+    assert len(sd.sdft_get_scf_log(ctx)) == 3
+    assert np.isfinite(r["energy"])
