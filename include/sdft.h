@@ -115,7 +115,7 @@ typedef struct {
     double energy;     /* Harris-Foulkes free energy at rho_in, Ha */
     double scf_error;  /* ||rho_out - rho_in|| / ||rho_out|| */
     double mu;         /* Fermi level */
-    double seconds;    /* wall time since the start of sdft_scf (stream-synchronised) */
+    double seconds;    /* device time (CUDA events) from the start of sdft_scf to the end of this iteration */
     double lower, cutoff, upper; /* filter bounds a0, a, b of the first problem */
 } sdft_iter_record;
 
@@ -228,6 +228,29 @@ sdft_status sdft_lanczos_bounds(sdft_ctx* ctx, int spin, int kpt, int steps, dou
 
 /* Number of kernel launches the library has issued on this context (for benchmarks). */
 sdft_status sdft_launch_count(const sdft_ctx* ctx, uint64_t* count);
+
+/* ---- tracing: per-kernel-family device time (paper Sec. 2.1 ".out ... various timings") -- */
+enum {
+    SDFT_K_STENCIL = 0,    /* fused H Y + Chebyshev step (bytes: Y, Yprev read + Ynext write) */
+    SDFT_K_KB_PROJECT = 1, /* KB projection C = beta^H Y */
+    SDFT_K_GRAM = 2,       /* M = Y^H Y, Hs = Y^H HY (flops: 4 ngrid ncol^2, complex x4) */
+    SDFT_K_EIGEN = 3,      /* equilibration + generalized eigensolve */
+    SDFT_K_ROTATE = 4,     /* X = Y Q (flops: 2 ngrid ncol^2, complex x4) */
+    SDFT_K_POISSON = 5,    /* AAR Poisson solve (whole solve) */
+    SDFT_K_DENSITY = 6,    /* density from orbitals */
+    SDFT_K_COUNT = 7
+};
+typedef struct {
+    uint64_t launches;     /* timed launches (or solves) */
+    double seconds;        /* summed device time between CUDA events around each launch */
+    double bytes;          /* summed algorithmic bytes moved (0 where not defined) */
+    double flops;          /* summed algorithmic flops (0 where not defined) */
+} sdft_kernel_stats;
+/* on != 0: record a CUDA event pair around every launch of the families above (adds ~2 us per
+ * launch); statistics accumulate until sdft_reset_kernel_stats. */
+sdft_status sdft_set_timing(sdft_ctx* ctx, int on);
+sdft_status sdft_get_kernel_stats(sdft_ctx* ctx, int family, sdft_kernel_stats* out);
+sdft_status sdft_reset_kernel_stats(sdft_ctx* ctx);
 
 #ifdef __cplusplus
 }

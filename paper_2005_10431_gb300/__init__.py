@@ -21,7 +21,8 @@ __all__ = [
     "sdft_set_density", "sdft_get_forces", "sdft_get_scf_log", "sdft_get_pseudocharge", "sdft_get_sad_density",
     "sdft_set_orbitals", "sdft_get_orbitals", "sdft_set_veff", "sdft_apply_h", "sdft_chebyshev_filter",
     "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
-    "sdft_lanczos_bounds", "sdft_launch_count", "pack_block", "unpack_block", "block_shape",
+    "sdft_lanczos_bounds", "sdft_launch_count", "sdft_set_timing", "sdft_get_kernel_stats",
+    "sdft_reset_kernel_stats", "pack_block", "unpack_block", "block_shape",
 ]
 
 
@@ -288,6 +289,24 @@ def sdft_launch_count(ctx: Context) -> int:
     n = C.c_uint64(0)
     _check(_lib.lib().sdft_launch_count(ctx.handle, C.byref(n)), ctx.handle)
     return n.value
+
+
+def sdft_set_timing(ctx: Context, on: bool = True):
+    _check(_lib.lib().sdft_set_timing(ctx.handle, 1 if on else 0), ctx.handle)
+
+
+def sdft_get_kernel_stats(ctx: Context) -> dict:
+    """{family name: {launches, seconds, bytes, flops}} for every kernel family."""
+    out = {}
+    for i, name in enumerate(_lib.KERNEL_FAMILIES):
+        st = _lib.sdft_kernel_stats()
+        _check(_lib.lib().sdft_get_kernel_stats(ctx.handle, i, C.byref(st)), ctx.handle)
+        out[name] = {f: getattr(st, f) for f, _ in _lib.sdft_kernel_stats._fields_}
+    return out
+
+
+def sdft_reset_kernel_stats(ctx: Context):
+    _check(_lib.lib().sdft_reset_kernel_stats(ctx.handle), ctx.handle)
 
 
 # ---- block storage marshalling (see the storage kinds in include/sdft.h) -----------------

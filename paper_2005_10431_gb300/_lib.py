@@ -66,6 +66,14 @@ class sdft_result(C.Structure):
                 ("t_poisson", C.c_double), ("t_other", C.c_double)]
 
 
+class sdft_kernel_stats(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("seconds", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
+
+
+SDFT_K_STENCIL, SDFT_K_KB_PROJECT, SDFT_K_GRAM, SDFT_K_EIGEN, SDFT_K_ROTATE, SDFT_K_POISSON, SDFT_K_DENSITY = range(7)
+KERNEL_FAMILIES = ["stencil", "kb_project", "gram", "eigen", "rotate", "poisson", "density"]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -106,6 +114,9 @@ SIGNATURES = {
     "sdft_lanczos_bounds": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]),
     "sdft_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "sdft_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "sdft_get_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(sdft_kernel_stats)]),
+    "sdft_reset_kernel_stats": (C.c_int, [C.c_void_p]),
 }
 
 

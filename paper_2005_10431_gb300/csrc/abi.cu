@@ -33,10 +33,60 @@ void ctx_free_all(sdft_ctx* c) {
         else cudaFree(p);
     }
     c->owned.clear();
+    for (const PendingTiming& p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    c->pending.clear();
+    for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+    c->ev_free.clear();
     if (c->hscal) {
         cudaFreeHost(c->hscal);
         c->hscal = nullptr;
     }
+}
+
+static cudaEvent_t take_event(sdft_ctx* c) {
+    if (!c->ev_free.empty()) {
+        cudaEvent_t e = c->ev_free.back();
+        c->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    SDFT_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+ScopedTimer::ScopedTimer(sdft_ctx* c_, int fam_, double bytes_, double flops_)
+    : c(c_), fam(fam_), bytes(bytes_), flops(flops_) {
+    if (!c->timing) return;
+    a = take_event(c);
+    b = take_event(c);
+    cudaEventRecord(a, c->stream);
+}
+
+ScopedTimer::~ScopedTimer() {
+    if (!a) return;
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back(PendingTiming{a, b, fam, bytes, flops});
+}
+
+void resolve_timing(sdft_ctx* c) {
+    if (c->pending.empty()) return;
+    SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    for (const PendingTiming& p : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            sdft_kernel_stats& k = c->kstat[p.fam];
+            k.launches += 1;
+            k.seconds += 1e-3 * ms;
+            k.bytes += p.bytes;
+            k.flops += p.flops;
+        }
+        c->ev_free.push_back(p.a);
+        c->ev_free.push_back(p.b);
+    }
+    c->pending.clear();
 }
 
 namespace {
@@ -526,6 +576,28 @@ sdft_status sdft_lanczos_bounds(sdft_ctx* c, int spin, int kpt, int steps, doubl
         SDFT_REQUIRE(spin >= 0 && spin < c->opt.nspin && kpt >= 0 && kpt < c->opt.nkpt && steps >= 2 && lower && upper,
                      SDFT_ERR_INVALID_ARG, "arguments");
         sdft::lanczos(c, spin, kpt, steps, lower, upper);
+    })
+}
+
+sdft_status sdft_set_timing(sdft_ctx* c, int on) {
+    SDFT_TRY(c, {
+        sdft::resolve_timing(c);
+        c->timing = on != 0;
+    })
+}
+
+sdft_status sdft_get_kernel_stats(sdft_ctx* c, int family, sdft_kernel_stats* out) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(family >= 0 && family < SDFT_K_COUNT && out, SDFT_ERR_INVALID_ARG, "family / pointer");
+        sdft::resolve_timing(c);
+        *out = c->kstat[family];
+    })
+}
+
+sdft_status sdft_reset_kernel_stats(sdft_ctx* c) {
+    SDFT_TRY(c, {
+        sdft::resolve_timing(c);
+        for (int k = 0; k < SDFT_K_COUNT; ++k) c->kstat[k] = sdft_kernel_stats{};
     })
 }
 

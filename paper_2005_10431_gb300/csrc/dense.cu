@@ -343,6 +343,7 @@ void subspace_gram(sdft_ctx* c, int precision, bool cplx, const void* Y, const v
     nsplit = (c->ng + chunk - 1) / chunk;
     SDFT_REQUIRE((size_t)(nsplit * 2 * nn * w) <= c->part_elems, SDFT_ERR_INVALID_ARG, "gram: partial buffer too small");
     dim3 grid(tiles, tiles, (unsigned)nsplit);
+    ScopedTimer timer(c, SDFT_K_GRAM, 0.0, 2.0 * (double)c->ng * ncol * ncol * (cplx ? 4.0 : 1.0));
     switch (kind) {
         case 0: gram_kernel<0><<<grid, 256, 0, c->stream>>>(Y, HY, ncol, c->ng, chunk, c->part); break;
         case 1: gram_kernel<1><<<grid, 256, 0, c->stream>>>(Y, HY, ncol, c->ng, chunk, c->part); break;
@@ -356,6 +357,7 @@ void subspace_gram(sdft_ctx* c, int precision, bool cplx, const void* Y, const v
 
 void generalized_eig(sdft_ctx* c, bool cplx, double* M, double* Hs, double* eig, int ncol) {
     const long long nn = (long long)ncol * ncol;
+    ScopedTimer timer(c, SDFT_K_EIGEN);
     diag_kernel<<<nb(ncol), 256, 0, c->stream>>>(M, c->dscale, ncol, cplx);
     scale_kernel<<<nb(nn), 256, 0, c->stream>>>(M, Hs, c->dscale, ncol, cplx);
     count_launch(c, 2);
@@ -383,6 +385,7 @@ void generalized_eig(sdft_ctx* c, bool cplx, double* M, double* Hs, double* eig,
 void rotate_block(sdft_ctx* c, int precision, bool cplx, const void* Y, const double* Q, void* X, int ncol) {
     const int kind = kind_of(precision, cplx);
     dim3 grid((unsigned)((c->ng + 63) / 64), (ncol + 31) / 32);
+    ScopedTimer timer(c, SDFT_K_ROTATE, 0.0, 2.0 * (double)c->ng * ncol * ncol * (cplx ? 4.0 : 1.0));
     const void* Qp = Q;
     if (precision != SDFT_FP64) {
         const long long nq = (long long)ncol * ncol * (cplx ? 2 : 1);

@@ -636,6 +636,7 @@ void veff_to_float(sdft_ctx* c, int spin) {
 // ---------------------------------------------------------------------------------------
 int poisson_aar(sdft_ctx* c, const double* f, double* phi, double tol, int max_iter) {
     const long long n = c->ng;
+    ScopedTimer timer(c, SDFT_K_POISSON);
     const double omega = 0.6, beta = 0.6;
     const int m = 7, p = 6;
     // workspace: rhs, r, xprev, fprev, X[m], F[m]
@@ -731,6 +732,7 @@ void density_accumulate(sdft_ctx* c, int precision, bool cplx, const void* X, co
                         double weight, double* rho) {
     const double scale = weight / c->dV;
     const unsigned nb = nblocks(c->ng);
+    ScopedTimer timer(c, SDFT_K_DENSITY, (double)block_elems_bytes(c, precision, cplx, ncol));
     if (precision == SDFT_FP64) {
         if (cplx) density_kernel<1><<<nb, 256, 0, c->stream>>>(X, occ, ncol, scale, c->ng, rho);
         else density_kernel<0><<<nb, 256, 0, c->stream>>>(X, occ, ncol, scale, c->ng, rho);

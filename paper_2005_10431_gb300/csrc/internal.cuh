@@ -71,6 +71,12 @@ struct KBTables {
     bool cplx = false;
 };
 
+struct PendingTiming {
+    cudaEvent_t a, b;
+    int fam;
+    double bytes, flops;
+};
+
 struct Problem {              // one (spin, k) eigenproblem
     int spin = 0, kpt = 0;
     bool cplx = false;
@@ -105,6 +111,10 @@ struct sdft_ctx {
     std::vector<void*> owned;
     cusolverDnHandle_t solver = nullptr;
     uint64_t launches = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<sdft::PendingTiming> pending;
+    sdft_kernel_stats kstat[SDFT_K_COUNT] = {};
 
     // grid fields (FP64)
     double* b = nullptr;          // pseudocharge
@@ -173,6 +183,18 @@ inline size_t block_elems_bytes(const sdft_ctx* c, int precision, bool cplx, int
     size_t per = precision == SDFT_FP64 ? (cplx ? 16 : 8) : (cplx ? 8 : 4);
     return per * (size_t)c->ng * (size_t)ncol;
 }
+
+// CUDA-event timing of one kernel family over the scope (no-op unless c->timing)
+struct ScopedTimer {
+    sdft_ctx* c;
+    int fam;
+    double bytes, flops;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ScopedTimer(sdft_ctx* c_, int fam_, double bytes_ = 0, double flops_ = 0);
+    ~ScopedTimer();
+};
+// accumulate finished event pairs into c->kstat (synchronises the stream)
+void resolve_timing(sdft_ctx* c);
 
 // ---- stencil.cu ----------------------------------------------------------------------
 // Ynext = alpha*(H Y - c Y) - beta*Yprev  for `ncolE` element-columns (see Elem).

@@ -399,6 +399,7 @@ void launch_variant(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, 
     const KBTables& kb = c->kb[kpt];
     const void* pval = std::is_same<S, float>::value ? (const void*)kb.pval32 : (const void*)kb.pval64;
     const bool prev = Yprev != nullptr, hasv = V != nullptr, haskb = kbC != nullptr && kb.S > 0;
+    ScopedTimer timer(c, SDFT_K_STENCIL, (double)ncolE * (double)c->ng * sizeof(E) * (prev ? 3.0 : 2.0));
 #define SDFT_STEP(P, K, VV, KN)                                                                      \
     cheb_step_kernel<E, CPLX, TX, TY, PF, P, K, VV, KN><<<grid, block, 0, c->stream>>>(               \
         Y, Yprev, Ynext, V, kbC, kb.pcnt, kb.patom, pval, A)
@@ -428,6 +429,7 @@ void launch_project_impl(sdft_ctx* c, int kpt, const E* Y, E* C, int ncolE) {
     if (kb.natom == 0 || ncolE == 0) return;
     constexpr int NC = 4;
     dim3 grid(kb.natom, (ncolE + NC - 1) / NC);
+    ScopedTimer timer(c, SDFT_K_KB_PROJECT);
     using S = typename Elem<E>::S;
     const void* val = std::is_same<S, float>::value ? (const void*)kb.val32 : (const void*)kb.val64;
     if (kb.cplx) {
