@@ -59,7 +59,7 @@ static cudaEvent_t take_event(sdft_ctx* c) {
 
 ScopedTimer::ScopedTimer(sdft_ctx* c_, int fam_, double bytes_, double flops_)
     : c(c_), fam(fam_), bytes(bytes_), flops(flops_) {
-    if (!c->timing) return;
+    if (!c || !c->timing) return;
     a = take_event(c);
     b = take_event(c);
     cudaEventRecord(a, c->stream);

@@ -64,7 +64,7 @@ struct KBTables {
     float* val32 = nullptr;   // same in float
     int S = 0;                // slots per grid point
     int* pcnt = nullptr;      // [ng]
-    int* patom = nullptr;     // [S*ng]
+    int* patom = nullptr;     // [S*ng] atom of slot s at point g, -1 if unused (sorted by atom)
     double* pval64 = nullptr; // [S*ng] (x2 complex)
     float* pval32 = nullptr;
     double* gamma = nullptr;  // [natom] E_kb * dV
@@ -112,6 +112,7 @@ struct sdft_ctx {
     cusolverDnHandle_t solver = nullptr;
     uint64_t launches = 0;
     bool timing = false;
+    int stencil_choice[4] = {-1, -1, -1, -1};  // autotuned variant per storage kind
     std::vector<cudaEvent_t> ev_free;
     std::vector<sdft::PendingTiming> pending;
     sdft_kernel_stats kstat[SDFT_K_COUNT] = {};
@@ -190,7 +191,7 @@ struct ScopedTimer {
     int fam;
     double bytes, flops;
     cudaEvent_t a = nullptr, b = nullptr;
-    ScopedTimer(sdft_ctx* c_, int fam_, double bytes_ = 0, double flops_ = 0);
+    ScopedTimer(sdft_ctx* c_, int fam_, double bytes_ = 0, double flops_ = 0);  // c_ null: no-op
     ~ScopedTimer();
 };
 // accumulate finished event pairs into c->kstat (synchronises the stream)

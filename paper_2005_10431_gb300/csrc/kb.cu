@@ -240,6 +240,7 @@ void build_kb_tables(sdft_ctx* c, int kpt) {
     if (S > 0) {
         const size_t ps = (size_t)S * c->ng;
         T.patom = (int*)ctx_alloc(c, sizeof(int) * ps);
+        SDFT_CUDA(cudaMemsetAsync(T.patom, 0xff, sizeof(int) * ps, c->stream));  // unused slots: atom -1
         T.pval64 = (double*)ctx_alloc(c, sizeof(double) * ps * vw);
         T.pval32 = (float*)ctx_alloc(c, sizeof(float) * ps * vw);
         int* pfill = (int*)ctx_alloc(c, sizeof(int) * c->ng);

@@ -1,17 +1,28 @@
 // Instantiations of the fused stencil / Chebyshev-step kernels (see stencil_impl.cuh)
-// for one element type per translation unit, so the variants compile in parallel.
+// for FP32 blocks (two lanes per element: an orbital pair, or re/im of a Bloch orbital).
 #include "stencil_impl.cuh"
 
 namespace sdft {
+namespace {
+// tile variants (TX x TY threads, prefetch planes, min blocks per SM) timed by the autotuner
+const StepLauncher<float2> kReal[] = {
+    &launch_variant<float2, false, 32, 8, 2, 2, 1>, &launch_variant<float2, false, 32, 8, 2, 1, 2>,
+    &launch_variant<float2, false, 32, 4, 2, 2, 2>, &launch_variant<float2, false, 32, 16, 2, 1, 1>};
+const StepLauncher<float2> kCplx[] = {&launch_variant<float2, true, 32, 8, 2, 2, 1>,
+                                      &launch_variant<float2, true, 32, 8, 2, 1, 2>};
+}  // namespace
 
 template <>
 void launch_cheb_step<float2>(sdft_ctx* c, int kpt, const float2* Y, const float2* Yprev, float2* Ynext, int ncolE,
                               const float* V, const float2* kbC, double alpha, double beta, double shift,
                               bool with_kinetic) {
-    if (c->kb[kpt].cplx)
-        launch_variant<float2, true, 32, 8, 2>(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, with_kinetic);
-    else
-        launch_variant<float2, false, 32, 8, 2>(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, with_kinetic);
+    const bool cplx = c->kb[kpt].cplx;
+    const StepLauncher<float2>* table = cplx ? kCplx : kReal;
+    const int nvar = cplx ? 2 : 4;
+    int& choice = c->stencil_choice[cplx ? 1 : 0];
+    if (choice < 0)
+        choice = autotune_stencil<float2>(c, table, nvar, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift);
+    table[choice](c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, with_kinetic, true);
 }
 
 template <>

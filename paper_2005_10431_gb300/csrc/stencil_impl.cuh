@@ -161,34 +161,47 @@ __device__ __forceinline__ E load_col(const E* __restrict__ Yc, const ColRef<E>&
     return v;
 }
 
-// KB scatter value at point g for element-column col
-template <typename E, typename S, bool CPLX>
-__device__ __forceinline__ E kb_term(long long g, int col, const int* __restrict__ pcnt,
-                                     const int* __restrict__ patom, const void* __restrict__ pval,
-                                     const E* __restrict__ C, long long ng, int natom) {
-    E acc = ezero<E>();
-    int cnt = __ldg(pcnt + g);
-    for (int s = 0; s < cnt; ++s) {
-        int a = __ldg(patom + s * ng + g);
-        E cv = C[(long long)col * natom + a];
-        if constexpr (CPLX) {
-            E bv = reinterpret_cast<const E*>(pval)[s * ng + g];
-            acc = eadd(acc, cmul(bv, cv));
-        } else {
-            S bv = reinterpret_cast<const S*>(pval)[s * ng + g];
-            acc = efma(bv, cv, acc);
-        }
+// Wrapped plane index advanced one plane at a time (no division in the loop): wz = z mod n3,
+// tz = floor(z / n3) (Bloch wrap count), off = wz * n1 * n2.
+struct ZTrack {
+    int wz, tz;
+    long long off;
+};
+__device__ __forceinline__ void ztrack_init(ZTrack& t, int z, int n3, long long plane) {
+    t.wz = wrapi(z, n3, t.tz);
+    t.off = (long long)t.wz * plane;
+}
+__device__ __forceinline__ void ztrack_next(ZTrack& t, int n3, long long plane) {
+    if (++t.wz == n3) {
+        t.wz = 0;
+        ++t.tz;
+        t.off = 0;
+    } else {
+        t.off += plane;
     }
-    return acc;
 }
 
-template <typename E, bool CPLX, int TX, int TY, int PF, bool PREV, bool KB, bool VLOC, bool KIN>
-__global__ void __launch_bounds__(TX * TY)
+template <typename E, typename S, bool CPLX>
+__device__ __forceinline__ E load_at(const E* __restrict__ Yc, long long idx, const E& colph, int tz,
+                                     const StepArgs<S>& A) {
+    E v = Yc[idx];
+    if constexpr (CPLX) {
+        v = cmul(v, colph);
+        if (tz) v = apply_phase<E, S>(v, tz, A.phr[2], A.phi[2]);
+    }
+    return v;
+}
+
+// One CTA: TX x TY grid columns, planes [z0, z1), NC element-columns (orbital pairs / Bloch
+// orbitals) per thread.
+template <typename E, bool CPLX, int TX, int TY, int PF, int MINB, int NC, bool PREV, bool KB, bool VLOC, bool KIN>
+__global__ void __launch_bounds__(TX * TY, MINB)
 cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __restrict__ Ynext,
                  const typename Elem<E>::S* __restrict__ V, const E* __restrict__ C,
-                 const int* __restrict__ pcnt, const int* __restrict__ patom,
-                 const void* __restrict__ pval, const StepArgs<typename Elem<E>::S> A) {
+                 const int* __restrict__ patom, const void* __restrict__ pval, const int nslot, const int ncolE,
+                 const StepArgs<typename Elem<E>::S> A) {
     using S = typename Elem<E>::S;
+    using KV = typename std::conditional<CPLX, E, S>::type;   // KB value type at a grid point
     constexpr int R = FD_RADIUS;
     constexpr int QN = 2 * R + 1 + PF;      // register queue length
     constexpr int HW = TX + 2 * R;          // smem tile width
@@ -196,18 +209,31 @@ cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __rest
     constexpr int NT = TX * TY;
     constexpr int NHALO = 2 * R * (TX + TY);
     constexpr int HPT = (NHALO + NT - 1) / NT;  // halo elements per thread
-    __shared__ E tile[2][HH][HW];
+    constexpr int SP = 3;                   // KB slots prefetched one plane ahead
+    __shared__ E tile[2][NC][HH][HW];
+    extern __shared__ unsigned char dyn_smem[];
+    E* Cs = reinterpret_cast<E*>(dyn_smem);  // KB coefficients of the NC columns, [NC][natom]
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int col = blockIdx.z / A.nzc;
-    const int zc = blockIdx.z - col * A.nzc;
+    const int cgrp = blockIdx.z / A.nzc;
+    const int zc = blockIdx.z - cgrp * A.nzc;
+    const int col0 = cgrp * NC;
     const int z0 = zc * A.zchunk;
     const int z1 = min(A.n3, z0 + A.zchunk);
     const int gx = x0 + tx, gy = y0 + ty;
     const bool valid = gx < A.n1 && gy < A.n2;
-    const E* __restrict__ Yc = Y + (long long)col * A.ng;
+    bool cval[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cval[c] = col0 + c < ncolE;
+    const long long plane = (long long)A.n1 * A.n2;
+    const KV* __restrict__ pv = reinterpret_cast<const KV*>(pval);
+    if (KB)
+        for (int i = tid; i < NC * A.natom; i += NT) {
+            const int c = i / A.natom, a = i - c * A.natom;
+            Cs[i] = col0 + c < ncolE ? C[(long long)(col0 + c) * A.natom + a] : ezero<E>();
+        }
 
     // halo slots owned by this thread: local (ly, lx) in the tile
     int hly[HPT], hlx[HPT];
@@ -231,64 +257,159 @@ cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __rest
         hcol[k] = make_col<E, S, CPLX>(x0 - R + hlx[k], y0 - R + max(hly[k], 0), A);
     }
     const ColRef<E> mycol = make_col<E, S, CPLX>(gx, gy, A);
+    const long long gxy = (long long)gy * A.n1 + gx;
 
-    E q[QN];
-    // prologue: planes z0-6 .. z0+5+PF  (queue slot s holds plane z0 - 6 + s + QN*m)
+    // per-point operands of the next plane, loaded one plane ahead (Yprev, V, KB slots)
+    E nprev[NC];
+    S nv = S(0);
+    int nat[SP];
+    KV nval[SP];
 #pragma unroll
-    for (int s = 0; s < 2 * R + PF; ++s)
-        q[s] = load_col<E, S, CPLX>(Yc, mycol, z0 - R + s, A);
-    E hreg[HPT];
+    for (int c = 0; c < NC; ++c) nprev[c] = ezero<E>();
 #pragma unroll
-    for (int k = 0; k < HPT; ++k)
-        if (hly[k] >= 0) hreg[k] = load_col<E, S, CPLX>(Yc, hcol[k], z0, A);
+    for (int s2 = 0; s2 < SP; ++s2) nat[s2] = -1;
+    auto fetch_point = [&](int z) {
+        if (!valid || z >= z1) return;
+        const long long g = (long long)z * plane + gxy;
+        if (PREV) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (cval[c]) nprev[c] = Yprev[(long long)(col0 + c) * A.ng + g];
+        }
+        if (VLOC) nv = __ldg(V + g);
+        if (KB) {
+#pragma unroll
+            for (int s2 = 0; s2 < SP; ++s2) {
+                if (s2 < nslot) {
+                    nat[s2] = __ldg(patom + s2 * A.ng + g);
+                    nval[s2] = pv[s2 * A.ng + g];
+                }
+            }
+        }
+    };
+
+    E q[NC][QN];
+    ZTrack zq;       // plane z + R + PF, the next queue load
+    ZTrack zh;       // plane z + 1, the next halo load
+    {
+        ZTrack t;
+        ztrack_init(t, z0 - R, A.n3, plane);
+#pragma unroll
+        for (int s2 = 0; s2 < 2 * R + PF; ++s2) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (cval[c])
+                    q[c][s2] = load_at<E, S, CPLX>(Y + (long long)(col0 + c) * A.ng, t.off + mycol.base, mycol.ph,
+                                                   t.tz, A);
+            ztrack_next(t, A.n3, plane);
+        }
+        zq = t;
+    }
+    E hreg[NC][HPT];
+    {
+        ZTrack t;
+        ztrack_init(t, z0, A.n3, plane);
+#pragma unroll
+        for (int k = 0; k < HPT; ++k)
+            if (hly[k] >= 0)
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    if (cval[c])
+                        hreg[c][k] = load_at<E, S, CPLX>(Y + (long long)(col0 + c) * A.ng, t.off + hcol[k].base,
+                                                         hcol[k].ph, t.tz, A);
+        ztrack_next(t, A.n3, plane);
+        zh = t;
+    }
+    fetch_point(z0);
 
     for (int zb = z0; zb < z1; zb += QN) {
 #pragma unroll
         for (int ph = 0; ph < QN; ++ph) {
             const int z = zb + ph;
             if (z < z1) {
-                E (*T)[HW] = tile[(z - z0) & 1];
+                const int buf = (z - z0) & 1;
                 // slot of plane z + dz is (ph + R + dz) mod QN
-                const E center = q[(ph + R) % QN];
-                T[R + ty][R + tx] = center;
 #pragma unroll
-                for (int k = 0; k < HPT; ++k)
-                    if (hly[k] >= 0) T[hly[k]][hlx[k]] = hreg[k];
-                // prefetch plane z + R + PF into the slot of plane z - R - 1
-                q[(ph + 2 * R + PF) % QN] = load_col<E, S, CPLX>(Yc, mycol, z + R + PF, A);
+                for (int c = 0; c < NC; ++c) {
+                    tile[buf][c][R + ty][R + tx] = q[c][(ph + R) % QN];
+#pragma unroll
+                    for (int k = 0; k < HPT; ++k)
+                        if (hly[k] >= 0) tile[buf][c][hly[k]][hlx[k]] = hreg[c][k];
+                }
+                // operands of this plane (prefetched), then issue the loads of later planes
+                E prev[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) prev[c] = nprev[c];
+                const S vloc = nv;
+                int at[SP];
+                KV val[SP];
+#pragma unroll
+                for (int s2 = 0; s2 < SP; ++s2) {
+                    at[s2] = nat[s2];
+                    val[s2] = nval[s2];
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    if (cval[c])
+                        q[c][(ph + 2 * R + PF) % QN] = load_at<E, S, CPLX>(Y + (long long)(col0 + c) * A.ng,
+                                                                           zq.off + mycol.base, mycol.ph, zq.tz, A);
+                ztrack_next(zq, A.n3, plane);
                 if (z + 1 < z1) {
 #pragma unroll
                     for (int k = 0; k < HPT; ++k)
                         if (hly[k] >= 0)
-                            hreg[k] = load_col<E, S, CPLX>(Yc, hcol[k], z + 1, A);
+#pragma unroll
+                            for (int c = 0; c < NC; ++c)
+                                if (cval[c])
+                                    hreg[c][k] = load_at<E, S, CPLX>(Y + (long long)(col0 + c) * A.ng,
+                                                                     zh.off + hcol[k].base, hcol[k].ph, zh.tz, A);
+                    ztrack_next(zh, A.n3, plane);
                 }
-                const long long g = ((long long)z * A.n2 + gy) * A.n1 + gx;
-                E prev = ezero<E>();
-                S vloc = S(0);
-                if (valid) {
-                    if (PREV) prev = Yprev[(long long)col * A.ng + g];
-                    if (VLOC) vloc = V[g];
-                }
+                fetch_point(z + 1);
                 __syncthreads();
                 if (valid) {
-                    E acc = ezero<E>();
-                    if (KIN) {
-                        acc = efma(A.c0, center, acc);
+                    const long long g = (long long)z * plane + gxy;
 #pragma unroll
-                        for (int r = 1; r <= R; ++r) {
-                            acc = efma(A.cz[r], eadd(q[(ph + R + r) % QN], q[(ph + R - r + QN) % QN]), acc);
-                            acc = efma(A.cx[r], eadd(T[R + ty][R + tx + r], T[R + ty][R + tx - r]), acc);
-                            acc = efma(A.cy[r], eadd(T[R + ty + r][R + tx], T[R + ty - r][R + tx]), acc);
+                    for (int c = 0; c < NC; ++c) {
+                        if (!cval[c]) continue;
+                        E (*T)[HW] = tile[buf][c];
+                        const E center = q[c][(ph + R) % QN];
+                        E acc = ezero<E>();
+                        if (KIN) {
+                            acc = efma(A.c0, center, acc);
+#pragma unroll
+                            for (int r = 1; r <= R; ++r) {
+                                acc = efma(A.cz[r], eadd(q[c][(ph + R + r) % QN], q[c][(ph + R - r + QN) % QN]), acc);
+                                acc = efma(A.cx[r], eadd(T[R + ty][R + tx + r], T[R + ty][R + tx - r]), acc);
+                                acc = efma(A.cy[r], eadd(T[R + ty + r][R + tx], T[R + ty - r][R + tx]), acc);
+                            }
                         }
+                        if (VLOC) acc = efma(vloc, center, acc);
+                        if (KB) {
+                            // sum_s beta_s(g) * C[atom_s]: slots are padded with atom -1
+                            const E* Cc = Cs + c * A.natom;
+#pragma unroll
+                            for (int s2 = 0; s2 < SP; ++s2) {
+                                if (s2 < nslot && at[s2] >= 0) {
+                                    if constexpr (CPLX) acc = eadd(acc, cmul(val[s2], Cc[at[s2]]));
+                                    else acc = efma(val[s2], Cc[at[s2]], acc);
+                                }
+                            }
+                            for (int s2 = SP; s2 < nslot; ++s2) {
+                                const int a2 = __ldg(patom + s2 * A.ng + g);
+                                if (a2 >= 0) {
+                                    if constexpr (CPLX) acc = eadd(acc, cmul(pv[s2 * A.ng + g], Cc[a2]));
+                                    else acc = efma(pv[s2 * A.ng + g], Cc[a2], acc);
+                                }
+                            }
+                        }
+                        // out = alpha * (acc - shift * center) - beta * prev
+                        E t = efma(-A.shift, center, acc);
+                        E out = ezero<E>();
+                        out = efma(A.alpha, t, out);
+                        if (PREV) out = efma(-A.beta, prev[c], out);
+                        Ynext[(long long)(col0 + c) * A.ng + g] = out;
                     }
-                    if (VLOC) acc = efma(vloc, center, acc);
-                    if (KB) acc = eadd(acc, kb_term<E, S, CPLX>(g, col, pcnt, patom, pval, C, A.ng, A.natom));
-                    // out = alpha * (acc - shift * center) - beta * prev
-                    E t = efma(-A.shift, center, acc);
-                    E out = ezero<E>();
-                    out = efma(A.alpha, t, out);
-                    if (PREV) out = efma(-A.beta, prev, out);
-                    Ynext[(long long)col * A.ng + g] = out;
                 }
             }
         }
@@ -354,6 +475,8 @@ kb_project_kernel(const E* __restrict__ Y, E* __restrict__ C, const int* __restr
     }
 }
 
+inline bool haskb_dsm(const void* kbC, const KBTables& kb) { return kbC != nullptr && kb.S > 0; }
+
 template <typename S>
 StepArgs<S> make_args(sdft_ctx* c, int kpt, double alpha, double beta, double shift, int zchunk, int nzc) {
     StepArgs<S> A;
@@ -381,28 +504,31 @@ StepArgs<S> make_args(sdft_ctx* c, int kpt, double alpha, double beta, double sh
     return A;
 }
 
-template <typename E, bool CPLX, int TX, int TY, int PF>
+template <typename E, bool CPLX, int TX, int TY, int PF, int MINB, int NC>
 void launch_variant(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, int ncolE,
                     const typename Elem<E>::S* V, const E* kbC, double alpha, double beta, double shift,
-                    bool kin) {
+                    bool kin, bool timed) {
     using S = typename Elem<E>::S;
     const int tiles = ((c->n[0] + TX - 1) / TX) * ((c->n[1] + TY - 1) / TY);
     // enough CTAs to fill 152 SMs several times over; each z chunk >= 16 planes
     long long want = 8LL * 152;
     int nzc = 1;
-    while ((long long)tiles * ncolE * nzc < want && c->n[2] / (nzc + 1) >= 16) ++nzc;
+    const int ngrp = (ncolE + NC - 1) / NC;
+    while ((long long)tiles * ngrp * nzc < want && c->n[2] / (nzc + 1) >= 16) ++nzc;
     const int zchunk = (c->n[2] + nzc - 1) / nzc;
     nzc = (c->n[2] + zchunk - 1) / zchunk;
     StepArgs<S> A = make_args<S>(c, kpt, alpha, beta, shift, zchunk, nzc);
-    dim3 grid((c->n[0] + TX - 1) / TX, (c->n[1] + TY - 1) / TY, (unsigned)(ncolE * nzc));
+    dim3 grid((c->n[0] + TX - 1) / TX, (c->n[1] + TY - 1) / TY, (unsigned)(ngrp * nzc));
     dim3 block(TX, TY);
     const KBTables& kb = c->kb[kpt];
     const void* pval = std::is_same<S, float>::value ? (const void*)kb.pval32 : (const void*)kb.pval64;
+    const size_t dsm = haskb_dsm(kbC, kb) ? sizeof(E) * (size_t)NC * std::max(1, c->natom) : 0;
     const bool prev = Yprev != nullptr, hasv = V != nullptr, haskb = kbC != nullptr && kb.S > 0;
-    ScopedTimer timer(c, SDFT_K_STENCIL, (double)ncolE * (double)c->ng * sizeof(E) * (prev ? 3.0 : 2.0));
+    ScopedTimer timer(timed ? c : nullptr, SDFT_K_STENCIL,
+                      (double)ncolE * (double)c->ng * sizeof(E) * (prev ? 3.0 : 2.0));
 #define SDFT_STEP(P, K, VV, KN)                                                                      \
-    cheb_step_kernel<E, CPLX, TX, TY, PF, P, K, VV, KN><<<grid, block, 0, c->stream>>>(               \
-        Y, Yprev, Ynext, V, kbC, kb.pcnt, kb.patom, pval, A)
+    cheb_step_kernel<E, CPLX, TX, TY, PF, MINB, NC, P, K, VV, KN><<<grid, block, dsm, c->stream>>>(   \
+        Y, Yprev, Ynext, V, kbC, kb.patom, pval, kb.S, ncolE, A)
     SDFT_REQUIRE(kin, SDFT_ERR_INVALID_ARG, "stencil step without kinetic term is not built");
     if (hasv) {
         if (prev && haskb) SDFT_STEP(true, true, true, true);
@@ -418,6 +544,45 @@ void launch_variant(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, 
 #undef SDFT_STEP
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);
+}
+
+template <typename E>
+using StepLauncher = void (*)(sdft_ctx*, int, const E*, const E*, E*, int, const typename Elem<E>::S*, const E*,
+                              double, double, double, bool, bool);
+
+// Stencil tile autotuner: time every compiled variant on the real operands (Ynext is rewritten by
+// the chosen variant afterwards) and keep the fastest for this context.  SDFT_STENCIL_VARIANT=k
+// forces variant k.  Small problems use variant 0 without timing.
+template <typename E>
+int autotune_stencil(sdft_ctx* c, const StepLauncher<E>* table, int nvar, int kpt, const E* Y, const E* Yprev,
+                     E* Ynext, int ncolE, const typename Elem<E>::S* V, const E* kbC, double alpha, double beta,
+                     double shift) {
+    if (const char* env = getenv("SDFT_STENCIL_VARIANT")) {
+        const int v = atoi(env);
+        if (v >= 0 && v < nvar) return v;
+    }
+    if (nvar == 1 || (double)c->ng * ncolE < 4e6) return 0;
+    cudaEvent_t a, b;
+    SDFT_CUDA(cudaEventCreate(&a));
+    SDFT_CUDA(cudaEventCreate(&b));
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int v = 0; v < nvar; ++v) {
+        table[v](c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, true, false);  // warm-up
+        SDFT_CUDA(cudaEventRecord(a, c->stream));
+        for (int r = 0; r < 3; ++r) table[v](c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, true, false);
+        SDFT_CUDA(cudaEventRecord(b, c->stream));
+        SDFT_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        SDFT_CUDA(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
 }
 
 

@@ -77,6 +77,30 @@ def test_apply_h_matches_oracle(sd, precision, kred):
     assert _relerr(got, ref) < tol
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("kred", [(0.0, 0.0, 0.0), (0.25, 0.0, -0.5)])
+def test_every_stencil_tile_variant_matches_oracle(sd, variant, kred, monkeypatch):
+    # The autotuner may pick any compiled tile shape; each one must give the same H X.
+    # 6 real states = 3 orbital pairs, so the two-column variants also run a ragged tail.
+    cplx = any(kred)
+    if cplx and variant > 1:
+        pytest.skip("complex blocks compile two variants")
+    monkeypatch.setenv("SDFT_STENCIL_VARIANT", str(variant))
+    cell = _ragged_cell()
+    ns = 6
+    ctx = _ctx(sd, cell, sd.SDFT_MIXED, ns, kpts=[kred] if cplx else None)
+    V = np.random.default_rng(11).normal(0, 0.4, cell.ngrid)
+    sd.sdft_set_veff(ctx, 0, V)
+    X = workloads.initial_orbitals(13, cell.ngrid, ns, complex_valued=cplx)
+    x = sd.pack_block(X, sd.SDFT_MIXED)
+    y = torch.empty_like(x)
+    sd.sdft_chebyshev_filter(ctx, 0, 0, sd.SDFT_MIXED, x, y, ns, 4, 3.0, 90.0, -1.5)
+    P = model.projectors(cell, kred)
+    ref = chefsi.chebyshev_filter(lambda Z: ham.apply_h(cell, Z, V, P, model.kb_energies(cell), kred), X, 4,
+                                  3.0, 90.0, -1.5)
+    assert _relerr(sd.unpack_block(y, sd.SDFT_MIXED, cplx), ref) < 3e-5 * 4
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_chebyshev_filter_matches_oracle(sd, precision):
     cell = _ragged_cell()
