@@ -219,6 +219,15 @@ void build_context(sdft_ctx* c) {
                                      ns, c->Hs, ns, c->Ms, ns, c->dscale, &lw);
     SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "sygvd workspace query failed");
     c->solver_lwork = std::max(c->solver_lwork, lw);
+    if (const char* env = getenv("SDFT_EIGEN")) c->eig_method = atoi(env);
+    cs = cusolverDnCreateSyevjInfo(&c->syevj_params);
+    SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "syevj info");
+    cusolverDnXsyevjSetTolerance(c->syevj_params, 1e-14);
+    cusolverDnXsyevjSetMaxSweeps(c->syevj_params, 30);
+    cs = cusolverDnDsygvj_bufferSize(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER,
+                                     ns, c->Hs, ns, c->Ms, ns, c->dscale, &lw, c->syevj_params);
+    SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "sygvj workspace query failed");
+    c->solver_lwork = std::max(c->solver_lwork, lw);
     c->solver_work = ctx_alloc(c, (size_t)c->solver_lwork * 16 + 256);
     // mixing history
     const long long nv = (long long)o.nspin * ng;
@@ -364,6 +373,7 @@ sdft_status sdft_create(const sdft_cell* cell, const sdft_grid* grid, const sdft
 void sdft_destroy(sdft_ctx* c) {
     if (!c) return;
     sdft::ctx_free_all(c);
+    if (c->syevj_params) cusolverDnDestroySyevjInfo(c->syevj_params);
     if (c->solver) cusolverDnDestroy(c->solver);
     delete c;
 }

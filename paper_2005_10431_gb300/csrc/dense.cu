@@ -362,7 +362,10 @@ void generalized_eig(sdft_ctx* c, bool cplx, double* M, double* Hs, double* eig,
     scale_kernel<<<nb(nn), 256, 0, c->stream>>>(M, Hs, c->dscale, ncol, cplx);
     count_launch(c, 2);
     cusolverStatus_t st;
-    if (cplx) {
+    if (c->eig_method == 1 && !cplx) {
+        st = cusolverDnDsygvj(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, ncol, Hs,
+                              ncol, M, ncol, eig, (double*)c->solver_work, c->solver_lwork, c->dinfo, c->syevj_params);
+    } else if (cplx) {
         st = cusolverDnZhegvd(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, ncol,
                               (cuDoubleComplex*)Hs, ncol, (cuDoubleComplex*)M, ncol, eig,
                               (cuDoubleComplex*)c->solver_work, c->solver_lwork, c->dinfo);

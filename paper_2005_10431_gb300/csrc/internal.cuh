@@ -110,6 +110,8 @@ struct sdft_ctx {
     void* alloc_user = nullptr;
     std::vector<void*> owned;
     cusolverDnHandle_t solver = nullptr;
+    syevjInfo_t syevj_params = nullptr;
+    int eig_method = 0;           // 0: sygvd/hegvd, 1: sygvj (real)
     uint64_t launches = 0;
     bool timing = false;
     int stencil_choice[4] = {-1, -1, -1, -1};  // autotuned variant per storage kind

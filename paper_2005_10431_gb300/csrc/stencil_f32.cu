@@ -5,11 +5,12 @@
 namespace sdft {
 namespace {
 // tile variants (TX x TY threads, prefetch planes, min blocks per SM) timed by the autotuner
+// (TX, TY, queue prefetch PF, min blocks per SM, cp.async stages D)
 const StepLauncher<float2> kReal[] = {
-    &launch_variant<float2, false, 32, 8, 2, 2, 1>, &launch_variant<float2, false, 32, 8, 2, 1, 2>,
-    &launch_variant<float2, false, 32, 4, 2, 2, 2>, &launch_variant<float2, false, 32, 16, 2, 1, 1>};
-const StepLauncher<float2> kCplx[] = {&launch_variant<float2, true, 32, 8, 2, 2, 1>,
-                                      &launch_variant<float2, true, 32, 8, 2, 1, 2>};
+    &launch_variant<float2, false, 32, 8, 2, 2, 4>, &launch_variant<float2, false, 32, 8, 3, 2, 3>,
+    &launch_variant<float2, false, 32, 16, 2, 1, 3>, &launch_variant<float2, false, 32, 4, 2, 4, 4>};
+const StepLauncher<float2> kCplx[] = {&launch_variant<float2, true, 32, 8, 2, 2, 4>,
+                                      &launch_variant<float2, true, 32, 8, 3, 2, 3>};
 }  // namespace
 
 template <>

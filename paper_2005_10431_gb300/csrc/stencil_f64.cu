@@ -8,7 +8,7 @@ template <>
 void launch_cheb_step<double>(sdft_ctx* c, int kpt, const double* Y, const double* Yprev, double* Ynext, int ncolE,
                               const double* V, const double* kbC, double alpha, double beta, double shift,
                               bool with_kinetic) {
-    launch_variant<double, false, 32, 8, 2, 1, 1>(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, with_kinetic,
+    launch_variant<double, false, 32, 8, 2, 1, 3>(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, with_kinetic,
                                               true);
 }
 

@@ -192,9 +192,31 @@ __device__ __forceinline__ E load_at(const E* __restrict__ Yc, long long idx, co
     return v;
 }
 
-// One CTA: TX x TY grid columns, planes [z0, z1), NC element-columns (orbital pairs / Bloch
-// orbitals) per thread.
-template <typename E, bool CPLX, int TX, int TY, int PF, int MINB, int NC, bool PREV, bool KB, bool VLOC, bool KIN>
+// ---- asynchronous global -> shared copies (cp.async, LDGSTS) ---------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(smem_dst)), "l"(gsrc), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Shared-memory stage of one z-plane: the x/y halo tile (interior filled from the register
+// queue), and the per-point operands Yprev, V and the KB slots of the TX x TY columns.
+template <typename E, typename S, typename KV, int TX, int TY, int SP>
+struct Stage {
+    E tile[TY + 2 * FD_RADIUS][TX + 2 * FD_RADIUS];
+    E prev[TY][TX];
+    S v[TY][TX];
+    int kat[SP][TY][TX];
+    KV kval[SP][TY][TX];
+};
+
+// One CTA: TX x TY grid columns, planes [z0, z1), one element-column (orbital pair / Bloch
+// orbital).  z-neighbours: register queue, loaded PF planes ahead.  x/y halo and per-point
+// operands: D-stage cp.async ring, issued D-1 planes ahead, one __syncthreads per plane.
+template <typename E, bool CPLX, int TX, int TY, int PF, int MINB, int D, bool PREV, bool KB, bool VLOC, bool KIN>
 __global__ void __launch_bounds__(TX * TY, MINB)
 cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __restrict__ Ynext,
                  const typename Elem<E>::S* __restrict__ V, const E* __restrict__ C,
@@ -204,36 +226,30 @@ cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __rest
     using KV = typename std::conditional<CPLX, E, S>::type;   // KB value type at a grid point
     constexpr int R = FD_RADIUS;
     constexpr int QN = 2 * R + 1 + PF;      // register queue length
-    constexpr int HW = TX + 2 * R;          // smem tile width
-    constexpr int HH = TY + 2 * R;
     constexpr int NT = TX * TY;
     constexpr int NHALO = 2 * R * (TX + TY);
     constexpr int HPT = (NHALO + NT - 1) / NT;  // halo elements per thread
-    constexpr int SP = 3;                   // KB slots prefetched one plane ahead
-    __shared__ E tile[2][NC][HH][HW];
-    extern __shared__ unsigned char dyn_smem[];
-    E* Cs = reinterpret_cast<E*>(dyn_smem);  // KB coefficients of the NC columns, [NC][natom]
+    constexpr int SP = 3;                   // KB slots staged per point (more are read directly)
+    using St = Stage<E, S, KV, TX, TY, SP>;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    St* stage = reinterpret_cast<St*>(dyn_smem);
+    E* Cs = reinterpret_cast<E*>(dyn_smem + sizeof(St) * D);  // KB coefficients of this column [natom]
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int cgrp = blockIdx.z / A.nzc;
-    const int zc = blockIdx.z - cgrp * A.nzc;
-    const int col0 = cgrp * NC;
+    const int col = blockIdx.z / A.nzc;
+    const int zc = blockIdx.z - col * A.nzc;
     const int z0 = zc * A.zchunk;
     const int z1 = min(A.n3, z0 + A.zchunk);
     const int gx = x0 + tx, gy = y0 + ty;
     const bool valid = gx < A.n1 && gy < A.n2;
-    bool cval[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) cval[c] = col0 + c < ncolE;
     const long long plane = (long long)A.n1 * A.n2;
+    const E* __restrict__ Yc = Y + (long long)col * A.ng;
+    const E* __restrict__ Pc = Yprev + (long long)col * A.ng;
     const KV* __restrict__ pv = reinterpret_cast<const KV*>(pval);
     if (KB)
-        for (int i = tid; i < NC * A.natom; i += NT) {
-            const int c = i / A.natom, a = i - c * A.natom;
-            Cs[i] = col0 + c < ncolE ? C[(long long)(col0 + c) * A.natom + a] : ezero<E>();
-        }
+        for (int i = tid; i < A.natom; i += NT) Cs[i] = C[(long long)col * A.natom + i];
 
     // halo slots owned by this thread: local (ly, lx) in the tile
     int hly[HPT], hlx[HPT];
@@ -259,161 +275,112 @@ cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __rest
     const ColRef<E> mycol = make_col<E, S, CPLX>(gx, gy, A);
     const long long gxy = (long long)gy * A.n1 + gx;
 
-    // per-point operands of the next plane, loaded one plane ahead (Yprev, V, KB slots)
-    E nprev[NC];
-    S nv = S(0);
-    int nat[SP];
-    KV nval[SP];
+    // issue the cp.async copies of plane z (always inside [0, n3): no z wrap) into stage st
+    auto issue = [&](int z, int st) {
+        if (z < z1) {
+            St& S_ = stage[st];
+            const long long off = (long long)z * plane;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) nprev[c] = ezero<E>();
+            for (int k = 0; k < HPT; ++k)
+                if (hly[k] >= 0) cp_async<sizeof(E)>(&S_.tile[hly[k]][hlx[k]], Yc + off + hcol[k].base);
+            if (valid) {
+                const long long g = off + gxy;
+                if (PREV) cp_async<sizeof(E)>(&S_.prev[ty][tx], Pc + g);
+                if (VLOC) cp_async<sizeof(S)>(&S_.v[ty][tx], V + g);
+                if (KB) {
 #pragma unroll
-    for (int s2 = 0; s2 < SP; ++s2) nat[s2] = -1;
-    auto fetch_point = [&](int z) {
-        if (!valid || z >= z1) return;
-        const long long g = (long long)z * plane + gxy;
-        if (PREV) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                if (cval[c]) nprev[c] = Yprev[(long long)(col0 + c) * A.ng + g];
-        }
-        if (VLOC) nv = __ldg(V + g);
-        if (KB) {
-#pragma unroll
-            for (int s2 = 0; s2 < SP; ++s2) {
-                if (s2 < nslot) {
-                    nat[s2] = __ldg(patom + s2 * A.ng + g);
-                    nval[s2] = pv[s2 * A.ng + g];
+                    for (int s2 = 0; s2 < SP; ++s2)
+                        if (s2 < nslot) {
+                            cp_async<4>(&S_.kat[s2][ty][tx], patom + s2 * A.ng + g);
+                            cp_async<sizeof(KV)>(&S_.kval[s2][ty][tx], pv + s2 * A.ng + g);
+                        }
                 }
             }
         }
+        cp_async_commit();  // one group per plane, possibly empty, keeps the group count uniform
     };
 
-    E q[NC][QN];
-    ZTrack zq;       // plane z + R + PF, the next queue load
-    ZTrack zh;       // plane z + 1, the next halo load
+    E q[QN];
+    ZTrack zq;   // plane z + R + PF, the next queue load
     {
         ZTrack t;
         ztrack_init(t, z0 - R, A.n3, plane);
 #pragma unroll
         for (int s2 = 0; s2 < 2 * R + PF; ++s2) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                if (cval[c])
-                    q[c][s2] = load_at<E, S, CPLX>(Y + (long long)(col0 + c) * A.ng, t.off + mycol.base, mycol.ph,
-                                                   t.tz, A);
+            q[s2] = load_at<E, S, CPLX>(Yc, t.off + mycol.base, mycol.ph, t.tz, A);
             ztrack_next(t, A.n3, plane);
         }
         zq = t;
     }
-    E hreg[NC][HPT];
-    {
-        ZTrack t;
-        ztrack_init(t, z0, A.n3, plane);
 #pragma unroll
-        for (int k = 0; k < HPT; ++k)
-            if (hly[k] >= 0)
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    if (cval[c])
-                        hreg[c][k] = load_at<E, S, CPLX>(Y + (long long)(col0 + c) * A.ng, t.off + hcol[k].base,
-                                                         hcol[k].ph, t.tz, A);
-        ztrack_next(t, A.n3, plane);
-        zh = t;
-    }
-    fetch_point(z0);
+    for (int d = 0; d < D - 1; ++d) issue(z0 + d, d);
 
     for (int zb = z0; zb < z1; zb += QN) {
 #pragma unroll
         for (int ph = 0; ph < QN; ++ph) {
             const int z = zb + ph;
             if (z < z1) {
-                const int buf = (z - z0) & 1;
-                // slot of plane z + dz is (ph + R + dz) mod QN
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    tile[buf][c][R + ty][R + tx] = q[c][(ph + R) % QN];
+                const int st = (z - z0) % D;
+                St& S_ = stage[st];
+                const E center = q[(ph + R) % QN];
+                // plane z: own copies complete, interior from the queue, Bloch phases on the halo
+                cp_async_wait<D - 2>();
+                S_.tile[R + ty][R + tx] = center;
+                if constexpr (CPLX) {
 #pragma unroll
                     for (int k = 0; k < HPT; ++k)
-                        if (hly[k] >= 0) tile[buf][c][hly[k]][hlx[k]] = hreg[c][k];
+                        if (hly[k] >= 0) S_.tile[hly[k]][hlx[k]] = cmul(S_.tile[hly[k]][hlx[k]], hcol[k].ph);
                 }
-                // operands of this plane (prefetched), then issue the loads of later planes
-                E prev[NC];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) prev[c] = nprev[c];
-                const S vloc = nv;
-                int at[SP];
-                KV val[SP];
-#pragma unroll
-                for (int s2 = 0; s2 < SP; ++s2) {
-                    at[s2] = nat[s2];
-                    val[s2] = nval[s2];
-                }
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    if (cval[c])
-                        q[c][(ph + 2 * R + PF) % QN] = load_at<E, S, CPLX>(Y + (long long)(col0 + c) * A.ng,
-                                                                           zq.off + mycol.base, mycol.ph, zq.tz, A);
+                // next queue plane (register prefetch PF planes ahead)
+                q[(ph + 2 * R + PF) % QN] = load_at<E, S, CPLX>(Yc, zq.off + mycol.base, mycol.ph, zq.tz, A);
                 ztrack_next(zq, A.n3, plane);
-                if (z + 1 < z1) {
-#pragma unroll
-                    for (int k = 0; k < HPT; ++k)
-                        if (hly[k] >= 0)
-#pragma unroll
-                            for (int c = 0; c < NC; ++c)
-                                if (cval[c])
-                                    hreg[c][k] = load_at<E, S, CPLX>(Y + (long long)(col0 + c) * A.ng,
-                                                                     zh.off + hcol[k].base, hcol[k].ph, zh.tz, A);
-                    ztrack_next(zh, A.n3, plane);
-                }
-                fetch_point(z + 1);
                 __syncthreads();
+                // every thread finished plane z-1: its stage takes plane z+D-1
+                issue(z + D - 1, (z - z0 + D - 1) % D);
                 if (valid) {
                     const long long g = (long long)z * plane + gxy;
+                    E acc = ezero<E>();
+                    if (KIN) {
+                        acc = efma(A.c0, center, acc);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        if (!cval[c]) continue;
-                        E (*T)[HW] = tile[buf][c];
-                        const E center = q[c][(ph + R) % QN];
-                        E acc = ezero<E>();
-                        if (KIN) {
-                            acc = efma(A.c0, center, acc);
-#pragma unroll
-                            for (int r = 1; r <= R; ++r) {
-                                acc = efma(A.cz[r], eadd(q[c][(ph + R + r) % QN], q[c][(ph + R - r + QN) % QN]), acc);
-                                acc = efma(A.cx[r], eadd(T[R + ty][R + tx + r], T[R + ty][R + tx - r]), acc);
-                                acc = efma(A.cy[r], eadd(T[R + ty + r][R + tx], T[R + ty - r][R + tx]), acc);
-                            }
+                        for (int r = 1; r <= R; ++r) {
+                            acc = efma(A.cz[r], eadd(q[(ph + R + r) % QN], q[(ph + R - r + QN) % QN]), acc);
+                            acc = efma(A.cx[r], eadd(S_.tile[R + ty][R + tx + r], S_.tile[R + ty][R + tx - r]), acc);
+                            acc = efma(A.cy[r], eadd(S_.tile[R + ty + r][R + tx], S_.tile[R + ty - r][R + tx]), acc);
                         }
-                        if (VLOC) acc = efma(vloc, center, acc);
-                        if (KB) {
-                            // sum_s beta_s(g) * C[atom_s]: slots are padded with atom -1
-                            const E* Cc = Cs + c * A.natom;
-#pragma unroll
-                            for (int s2 = 0; s2 < SP; ++s2) {
-                                if (s2 < nslot && at[s2] >= 0) {
-                                    if constexpr (CPLX) acc = eadd(acc, cmul(val[s2], Cc[at[s2]]));
-                                    else acc = efma(val[s2], Cc[at[s2]], acc);
-                                }
-                            }
-                            for (int s2 = SP; s2 < nslot; ++s2) {
-                                const int a2 = __ldg(patom + s2 * A.ng + g);
-                                if (a2 >= 0) {
-                                    if constexpr (CPLX) acc = eadd(acc, cmul(pv[s2 * A.ng + g], Cc[a2]));
-                                    else acc = efma(pv[s2 * A.ng + g], Cc[a2], acc);
-                                }
-                            }
-                        }
-                        // out = alpha * (acc - shift * center) - beta * prev
-                        E t = efma(-A.shift, center, acc);
-                        E out = ezero<E>();
-                        out = efma(A.alpha, t, out);
-                        if (PREV) out = efma(-A.beta, prev[c], out);
-                        Ynext[(long long)(col0 + c) * A.ng + g] = out;
                     }
+                    if (VLOC) acc = efma(S_.v[ty][tx], center, acc);
+                    if (KB) {
+                        // sum_s beta_s(g) * C[atom_s]: slots are padded with atom -1
+#pragma unroll
+                        for (int s2 = 0; s2 < SP; ++s2) {
+                            if (s2 < nslot) {
+                                const int a2 = S_.kat[s2][ty][tx];
+                                if (a2 >= 0) {
+                                    if constexpr (CPLX) acc = eadd(acc, cmul(S_.kval[s2][ty][tx], Cs[a2]));
+                                    else acc = efma(S_.kval[s2][ty][tx], Cs[a2], acc);
+                                }
+                            }
+                        }
+                        for (int s2 = SP; s2 < nslot; ++s2) {
+                            const int a2 = __ldg(patom + s2 * A.ng + g);
+                            if (a2 >= 0) {
+                                if constexpr (CPLX) acc = eadd(acc, cmul(pv[s2 * A.ng + g], Cs[a2]));
+                                else acc = efma(pv[s2 * A.ng + g], Cs[a2], acc);
+                            }
+                        }
+                    }
+                    // out = alpha * (acc - shift * center) - beta * prev
+                    E t = efma(-A.shift, center, acc);
+                    E out = ezero<E>();
+                    out = efma(A.alpha, t, out);
+                    if (PREV) out = efma(-A.beta, S_.prev[ty][tx], out);
+                    Ynext[(long long)col * A.ng + g] = out;
                 }
             }
         }
     }
+    cp_async_wait<0>();
 }
 
 // KB projection: C[col][a] = gamma_a * sum_j conj(beta_a(j)) Y[idx_j, col], NC columns per CTA
@@ -504,7 +471,7 @@ StepArgs<S> make_args(sdft_ctx* c, int kpt, double alpha, double beta, double sh
     return A;
 }
 
-template <typename E, bool CPLX, int TX, int TY, int PF, int MINB, int NC>
+template <typename E, bool CPLX, int TX, int TY, int PF, int MINB, int D>
 void launch_variant(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, int ncolE,
                     const typename Elem<E>::S* V, const E* kbC, double alpha, double beta, double shift,
                     bool kin, bool timed) {
@@ -513,7 +480,7 @@ void launch_variant(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, 
     // enough CTAs to fill 152 SMs several times over; each z chunk >= 16 planes
     long long want = 8LL * 152;
     int nzc = 1;
-    const int ngrp = (ncolE + NC - 1) / NC;
+    const int ngrp = ncolE;
     while ((long long)tiles * ngrp * nzc < want && c->n[2] / (nzc + 1) >= 16) ++nzc;
     const int zchunk = (c->n[2] + nzc - 1) / nzc;
     nzc = (c->n[2] + zchunk - 1) / zchunk;
@@ -522,13 +489,19 @@ void launch_variant(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, 
     dim3 block(TX, TY);
     const KBTables& kb = c->kb[kpt];
     const void* pval = std::is_same<S, float>::value ? (const void*)kb.pval32 : (const void*)kb.pval64;
-    const size_t dsm = haskb_dsm(kbC, kb) ? sizeof(E) * (size_t)NC * std::max(1, c->natom) : 0;
+    using KV = typename std::conditional<CPLX, E, S>::type;
+    const size_t dsm = sizeof(Stage<E, S, KV, TX, TY, 3>) * D +
+                       (haskb_dsm(kbC, kb) ? sizeof(E) * (size_t)std::max(1, c->natom) : 0);
     const bool prev = Yprev != nullptr, hasv = V != nullptr, haskb = kbC != nullptr && kb.S > 0;
     ScopedTimer timer(timed ? c : nullptr, SDFT_K_STENCIL,
                       (double)ncolE * (double)c->ng * sizeof(E) * (prev ? 3.0 : 2.0));
 #define SDFT_STEP(P, K, VV, KN)                                                                      \
-    cheb_step_kernel<E, CPLX, TX, TY, PF, MINB, NC, P, K, VV, KN><<<grid, block, dsm, c->stream>>>(   \
-        Y, Yprev, Ynext, V, kbC, kb.patom, pval, kb.S, ncolE, A)
+    do {                                                                                             \
+        auto kfn = cheb_step_kernel<E, CPLX, TX, TY, PF, MINB, D, P, K, VV, KN>;                      \
+        if (dsm > 48 * 1024)                                                                         \
+            SDFT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm)); \
+        kfn<<<grid, block, dsm, c->stream>>>(Y, Yprev, Ynext, V, kbC, kb.patom, pval, kb.S, ncolE, A); \
+    } while (0)
     SDFT_REQUIRE(kin, SDFT_ERR_INVALID_ARG, "stencil step without kinetic term is not built");
     if (hasv) {
         if (prev && haskb) SDFT_STEP(true, true, true, true);

@@ -8,7 +8,7 @@ template <>
 void launch_cheb_step<double2>(sdft_ctx* c, int kpt, const double2* Y, const double2* Yprev, double2* Ynext, int ncolE,
                                const double* V, const double2* kbC, double alpha, double beta, double shift,
                                bool with_kinetic) {
-    launch_variant<double2, true, 32, 8, 2, 1, 1>(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, with_kinetic,
+    launch_variant<double2, true, 32, 8, 2, 1, 3>(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, with_kinetic,
                                               true);
 }
 
