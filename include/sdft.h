@@ -146,6 +146,8 @@ sdft_status sdft_create(const sdft_cell* cell, const sdft_grid* grid, const sdft
                         sdft_alloc_fn alloc, sdft_free_fn free_fn, void* alloc_user,
                         void* cuda_stream, sdft_ctx** out);
 void sdft_destroy(sdft_ctx* ctx);
+/* Message of the last error on ctx; with ctx NULL, of the last failed sdft_create or
+ * context-free call on this thread. */
 const char* sdft_last_error(const sdft_ctx* ctx);
 
 /* ---- full SCF (paper Sec. 2.1) ------------------------------------------------------ */
@@ -203,6 +205,28 @@ sdft_status sdft_rayleigh_ritz(sdft_ctx* ctx, int spin, int kpt, int precision,
  * column-major; complex problems write double2).  hy is the device block H Y. */
 sdft_status sdft_subspace_matrices(sdft_ctx* ctx, int kpt, int precision, const void* y,
                                    const void* hy, void* m, void* hs, int ncol);
+
+/* Allocation-free variant of sdft_subspace_matrices, for callers that must not allocate device
+ * memory: code that runs while a CUDA graph is being captured in global mode (cudaMalloc fails
+ * then), hosts whose device memory is owned by their own pool allocator, and latency-critical
+ * loops where an allocation (which can synchronise the device) is not acceptable.  The paper has
+ * no counterpart; this is an interface convenience of this library.
+ *
+ * Computes the same M = Y^H Y and Hs = Y^H (H Y) (FP64 ncol x ncol, column-major, double2 for
+ * complex) from device blocks y, hy of ngrid x ncol in the storage kind of (precision,
+ * is_complex), with the same kernels, enqueued on cuda_stream (a cudaStream_t, NULL = default
+ * stream); no context is needed and nothing is allocated.  The split-K partial sums use a fixed
+ * 32 MiB device array inside the library, so 2*ncol^2*(2 if complex) must not exceed 4194304
+ * doubles (ncol <= 1448 real, <= 1024 complex); larger ncol returns SDFT_ERR_INVALID_ARG before
+ * anything is launched.  The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make it before any stream capture.  All calls
+ * share the one array per device and it keeps the last call's contents (every partial sum a call
+ * reads is written by that call first): calls whose kernels overlap on the GPU (other streams,
+ * other host threads) race and give wrong results.  Asynchronous; errors are reported by
+ * sdft_last_error(NULL). */
+sdft_status sdft_subspace_matrices_noalloc(int precision, int is_complex, const void* y, const void* hy,
+                                           int64_t ngrid, int ncol, double* m, double* hs,
+                                           void* cuda_stream);
 
 /* Rotation x = y Q for an FP64 ncol x ncol column-major Q (double2 for complex), device. */
 sdft_status sdft_rotate(sdft_ctx* ctx, int kpt, int precision, const void* y, const void* q,

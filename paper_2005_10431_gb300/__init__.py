@@ -20,7 +20,7 @@ __all__ = [
     "sdft_scf", "sdft_reset", "sdft_get_eigenvalues", "sdft_get_occupations", "sdft_get_density",
     "sdft_set_density", "sdft_get_forces", "sdft_get_scf_log", "sdft_get_pseudocharge", "sdft_get_sad_density",
     "sdft_set_orbitals", "sdft_get_orbitals", "sdft_set_veff", "sdft_apply_h", "sdft_chebyshev_filter",
-    "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
+    "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_subspace_matrices_noalloc", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
     "sdft_lanczos_bounds", "sdft_launch_count", "sdft_set_timing", "sdft_get_kernel_stats",
     "sdft_reset_kernel_stats", "pack_block", "unpack_block", "block_shape",
 ]
@@ -254,6 +254,16 @@ def sdft_rayleigh_ritz(ctx: Context, spin: int, kpt: int, precision: int, y, x, 
 def sdft_subspace_matrices(ctx: Context, kpt: int, precision: int, y, hy, m, hs, ncol: int):
     _check(_lib.lib().sdft_subspace_matrices(ctx.handle, kpt, precision, _ptr(y), _ptr(hy), _ptr(m), _ptr(hs),
                                              ncol), ctx.handle)
+    return m, hs
+
+
+def sdft_subspace_matrices_noalloc(precision: int, is_complex: bool, y, hy, ngrid: int, ncol: int, m, hs,
+                                   stream=None):
+    """Allocation-free M = Y^H Y, Hs = Y^H HY (no context; fixed library scratch, see sdft.h)."""
+    import torch
+    s = torch.cuda.current_stream().cuda_stream if stream is None else getattr(stream, "cuda_stream", stream)
+    _check(_lib.lib().sdft_subspace_matrices_noalloc(precision, 1 if is_complex else 0, _ptr(y), _ptr(hy), ngrid,
+                                                     ncol, _ptr(m), _ptr(hs), C.c_void_p(s)), None)
     return m, hs
 
 

@@ -589,6 +589,24 @@ sdft_status sdft_lanczos_bounds(sdft_ctx* c, int spin, int kpt, int steps, doubl
     })
 }
 
+sdft_status sdft_subspace_matrices_noalloc(int precision, int is_complex, const void* y, const void* hy,
+                                           int64_t ngrid, int ncol, double* m, double* hs, void* cuda_stream) {
+    try {
+        sdft::g_create_error.clear();
+        SDFT_REQUIRE(precision == SDFT_FP64 || precision == SDFT_MIXED, SDFT_ERR_INVALID_ARG, "precision");
+        SDFT_REQUIRE(y && hy && m && hs, SDFT_ERR_INVALID_ARG, "null pointer");
+        SDFT_REQUIRE(ngrid >= 1 && ncol >= 1, SDFT_ERR_INVALID_ARG, "ngrid and ncol must be >= 1");
+        SDFT_REQUIRE(precision == SDFT_FP64 || is_complex || ncol % 2 == 0, SDFT_ERR_INVALID_ARG,
+                     "SDFT_MIXED real blocks need an even column count");
+        sdft::subspace_gram_noalloc(precision, is_complex != 0, y, hy, (long long)ngrid, ncol, m, hs,
+                                    (cudaStream_t)cuda_stream);
+        return SDFT_OK;
+    } catch (const Error& e) {
+        sdft::g_create_error = e.msg;
+        return e.code;
+    }
+}
+
 sdft_status sdft_set_timing(sdft_ctx* c, int on) {
     SDFT_TRY(c, {
         sdft::resolve_timing(c);

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 namespace sdft {
 namespace {
@@ -325,7 +326,65 @@ __global__ void convert_kernel(const void* __restrict__ src, void* __restrict__ 
 inline int kind_of(int precision, bool cplx) { return precision == SDFT_FP64 ? (cplx ? 1 : 0) : (cplx ? 3 : 2); }
 inline unsigned nb(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16); }
 
+// ---------------------------------------------------------------------------------------
+// Fixed device scratch of the allocation-free Gram entry point: the split-K partial sums live
+// in this file-scope array instead of memory from cudaMalloc.  Every device that loads the
+// library holds it (32 MiB) until the process exits.  In host code the symbol is only a
+// stand-in; its device address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------------------
+constexpr size_t kNoAllocGramDoubles = size_t(1) << 22;
+static __device__ __align__(256) double g_noalloc_gram_scratch[kNoAllocGramDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device (set-up on the first call per device).
+double* noalloc_scratch() {
+    int dev = 0;
+    SDFT_CUDA(cudaGetDevice(&dev));
+    SDFT_REQUIRE(dev >= 0 && dev < kMaxDevices, SDFT_ERR_INVALID_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        SDFT_CUDA(cudaGetSymbolAddress(&p, g_noalloc_gram_scratch));
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    return g_noalloc_ptr[dev];
+}
+
 }  // namespace
+
+// M = Y^H Y, Hs = Y^H HY with the split-K partials in the fixed scratch above; launches the
+// same kernels as subspace_gram on `stream` and allocates nothing.
+void subspace_gram_noalloc(int precision, bool cplx, const void* Y, const void* HY, long long ng, int ncol,
+                           double* M, double* Hs, cudaStream_t stream) {
+    const int w = cplx ? 2 : 1;
+    const long long nn = (long long)ncol * ncol;
+    const long long per_split = 2 * nn * w;
+    SDFT_REQUIRE(per_split <= (long long)kNoAllocGramDoubles, SDFT_ERR_INVALID_ARG,
+                 "ncol too large for the fixed scratch of the allocation-free Gram: 2*ncol^2*(2 if complex) must be "
+                 "<= 4194304 (ncol <= 1448 real, <= 1024 complex)");
+    double* part = noalloc_scratch();
+    const int kind = kind_of(precision, cplx);
+    const int tiles = (ncol + GT - 1) / GT;
+    const long long tri = (long long)tiles * (tiles + 1) / 2;
+    long long nsplit = std::max<long long>(1, (4LL * 152 * 4) / std::max<long long>(1, tri));
+    nsplit = std::min<long long>(nsplit, (long long)kNoAllocGramDoubles / per_split);
+    nsplit = std::max<long long>(1, std::min<long long>(nsplit, (ng + GK - 1) / GK));
+    long long chunk = (ng + nsplit - 1) / nsplit;
+    chunk = (chunk + GK - 1) / GK * GK;
+    nsplit = (ng + chunk - 1) / chunk;
+    dim3 grid(tiles, tiles, (unsigned)nsplit);
+    switch (kind) {
+        case 0: gram_kernel<0><<<grid, 256, 0, stream>>>(Y, HY, ncol, ng, chunk, part); break;
+        case 1: gram_kernel<1><<<grid, 256, 0, stream>>>(Y, HY, ncol, ng, chunk, part); break;
+        case 2: gram_kernel<2><<<grid, 256, 0, stream>>>(Y, HY, ncol, ng, chunk, part); break;
+        default: gram_kernel<3><<<grid, 256, 0, stream>>>(Y, HY, ncol, ng, chunk, part); break;
+    }
+    gram_reduce_kernel<<<nb(nn), 256, 0, stream>>>(part, (int)nsplit, ncol, cplx, M, Hs);
+    SDFT_CUDA(cudaGetLastError());
+}
 
 void subspace_gram(sdft_ctx* c, int precision, bool cplx, const void* Y, const void* HY, double* M, double* Hs,
                    int ncol) {

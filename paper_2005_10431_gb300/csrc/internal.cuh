@@ -235,6 +235,9 @@ void forces_compute(sdft_ctx* c);
 // M = Y^H Y, Hs = Y^H HY (FP64 results, column-major ncol x ncol, x2 for complex)
 void subspace_gram(sdft_ctx* c, int precision, bool cplx, const void* Y, const void* HY,
                    double* M, double* Hs, int ncol);
+// allocation-free variant: partials in a fixed file-scope device array (no context needed)
+void subspace_gram_noalloc(int precision, bool cplx, const void* Y, const void* HY, long long ng, int ncol,
+                           double* M, double* Hs, cudaStream_t stream);
 // solve Hs q = lambda M q (FP64); Q overwrites Hs; eig ascending; throws CHOLESKY on failure
 void generalized_eig(sdft_ctx* c, bool cplx, double* M, double* Hs, double* eig, int ncol);
 // X = Y Q (Q FP64 column-major)
