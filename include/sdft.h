@@ -234,7 +234,9 @@ sdft_status sdft_rotate(sdft_ctx* ctx, int kpt, int precision, const void* y, co
 
 /* Poisson: -L phi = 4 pi (f - mean f), zero-mean phi, by AAR (paper Sec. 2.1; Pratapa,
  * Suryanarayana & Pask 2016).  f, phi: device FP64 [ngrid]; phi is also the initial guess.
- * *iters receives the iteration count.  NOT_CONVERGED if the tolerance is not reached. */
+ * tol bounds the FP64 relative residual.  FP64 contexts iterate in FP64; SDFT_MIXED contexts use
+ * FP64 residuals with FP32 AAR correction solves (iterative refinement), same tolerance.
+ * *iters receives the (inner) iteration count.  NOT_CONVERGED if the tolerance is not reached. */
 sdft_status sdft_poisson(sdft_ctx* ctx, const double* f, double* phi, double tol, int max_iter,
                          int* iters);
 

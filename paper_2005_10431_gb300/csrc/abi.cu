@@ -154,6 +154,7 @@ void build_context(sdft_ctx* c) {
     c->veff32 = (float*)ctx_alloc(c, sizeof(float) * o.nspin * ng);
     c->exc = (double*)ctx_alloc(c, sizeof(double) * ng);
     c->work64 = (double*)ctx_alloc(c, sizeof(double) * 28 * ng);
+    c->work32 = (float*)ctx_alloc(c, sizeof(float) * 20 * ng);
     // FD coefficients of -1/2 L_h
     const double w[7] = {-5369.0 / 1800.0, 12.0 / 7.0, -15.0 / 56.0, 10.0 / 189.0, -1.0 / 112.0, 2.0 / 1925.0,
                          -1.0 / 16632.0};
@@ -554,7 +555,8 @@ sdft_status sdft_rotate(sdft_ctx* c, int kpt, int precision, const void* y, cons
 sdft_status sdft_poisson(sdft_ctx* c, const double* f, double* phi, double tol, int max_iter, int* iters) {
     SDFT_TRY(c, {
         SDFT_REQUIRE(f && phi && tol > 0 && max_iter >= 1, SDFT_ERR_INVALID_ARG, "arguments");
-        const int it = sdft::poisson_aar(c, f, phi, tol, max_iter);
+        const int it = c->opt.precision == SDFT_MIXED ? sdft::poisson_mixed(c, f, phi, tol, max_iter)
+                                                      : sdft::poisson_aar(c, f, phi, tol, max_iter);
         SDFT_CUDA(cudaStreamSynchronize(c->stream));
         if (iters) *iters = it < 0 ? -it : it;
         if (it < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Poisson AAR did not reach the tolerance"};

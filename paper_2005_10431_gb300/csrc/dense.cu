@@ -195,23 +195,6 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nsplit, 
 }
 
 // D^-1/2 scaling of M and Hs with D = diag(M)
-__global__ void equilibrate_kernel(double* __restrict__ M, double* __restrict__ Hs, double* __restrict__ d, int n,
-                                   int cplx) {
-    const int w = cplx ? 2 : 1;
-    // d computed by every thread from the diagonal (cheap, n <= few thousand)
-    const long long nn = (long long)n * n;
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < nn; o += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(o % n), j = (int)(o / n);
-        const double di = rsqrt(M[w * ((long long)i + (long long)i * n)]);
-        const double dj = rsqrt(M[w * ((long long)j + (long long)j * n)]);
-        for (int q = 0; q < w; ++q) {
-            M[w * o + q] *= di * dj;
-            Hs[w * o + q] *= di * dj;
-        }
-        if (i == j) d[i] = di;
-    }
-}
-
 __global__ void diag_kernel(const double* __restrict__ M, double* __restrict__ d, int n, int cplx) {
     const int w = cplx ? 2 : 1;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)

@@ -11,7 +11,6 @@ namespace sdft {
 namespace {
 
 constexpr int RB = 256;   // reduction block size
-constexpr int RGRID = 512; // reduction blocks
 
 // ---------------------------------------------------------------------------------------
 // set-up: pseudocharge b and SAD density, summed over periodic images within the cutoff
@@ -170,22 +169,21 @@ __global__ void veff_kernel(int nspin, const double* __restrict__ phi, const dou
 // ---------------------------------------------------------------------------------------
 // elementwise helpers
 // ---------------------------------------------------------------------------------------
-__global__ void axpby_kernel(double* __restrict__ y, const double* __restrict__ x, double a, double b, long long n) {
+template <typename T>
+__global__ void axpby_kernel(T* __restrict__ y, const T* __restrict__ x, T a, T b, long long n) {
     // y = a*x + b*y
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = a * x[i] + b * y[i];
 }
+template <typename T, typename U>
+__global__ void convert_add_kernel(T* __restrict__ y, const U* __restrict__ x, double a, double b, long long n) {
+    // y = a*x + b*y with a type conversion (FP64 <-> FP32 vectors of the Poisson refinement)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (T)(a * (double)x[i] + b * (double)y[i]);
+}
 __global__ void to_float_grid_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
-}
-__global__ void sum_spins_plus_kernel(const double* __restrict__ rho, int nspin, const double* __restrict__ add,
-                                      double* __restrict__ out, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double s = add ? add[i] : 0.0;
-        for (int k = 0; k < nspin; ++k) s += rho[k * n + i];
-        out[i] = s;
-    }
 }
 __global__ void add_scalar_kernel(double* __restrict__ y, const double* __restrict__ s, double scale, long long n) {
     const double v = scale * s[0];
@@ -194,11 +192,12 @@ __global__ void add_scalar_kernel(double* __restrict__ y, const double* __restri
 }
 
 // Anderson history push: X[slot] = x - xprev, F[slot] = c*f - fprev; xprev = x, fprev = c*f
-__global__ void anderson_push_kernel(const double* __restrict__ x, const double* __restrict__ f, double c,
-                                     double* __restrict__ xprev, double* __restrict__ fprev, double* __restrict__ Xs,
-                                     double* __restrict__ Fs, int have_prev, long long n) {
+template <typename T>
+__global__ void anderson_push_kernel(const T* __restrict__ x, const T* __restrict__ f, T c, T* __restrict__ xprev,
+                                     T* __restrict__ fprev, T* __restrict__ Xs, T* __restrict__ Fs, int have_prev,
+                                     long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double fi = c * f[i];
+        const T fi = c * f[i];
         if (have_prev) {
             Xs[i] = x[i] - xprev[i];
             Fs[i] = fi - fprev[i];
@@ -209,31 +208,32 @@ __global__ void anderson_push_kernel(const double* __restrict__ x, const double*
 }
 
 // x += a*c*f - sum_j gamma_j (X_j + a F_j)   (gamma in device memory, m terms)
-__global__ void anderson_update_kernel(double* __restrict__ x, const double* __restrict__ f, double c, double a,
-                                       const double* __restrict__ X, const double* __restrict__ F,
-                                       const int* __restrict__ slots, const double* __restrict__ gamma, int m,
-                                       long long n) {
+template <typename T>
+__global__ void anderson_update_kernel(T* __restrict__ x, const T* __restrict__ f, T c, T a, const T* __restrict__ X,
+                                       const T* __restrict__ F, const int* __restrict__ slots,
+                                       const double* __restrict__ gamma, int m, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double v = x[i] + a * c * f[i];
+        T v = x[i] + a * c * f[i];
         for (int j = 0; j < m; ++j) {
             const long long o = (long long)slots[j] * n + i;
-            v -= gamma[j] * (X[o] + a * F[o]);
+            v -= (T)gamma[j] * (X[o] + a * F[o]);
         }
         x[i] = v;
     }
 }
 
 // Gram of the history: G[i][j] = F_i . F_j (i <= j), r_i = F_i . (c f), plus f.f; partials per block
-__global__ void anderson_gram_kernel(const double* __restrict__ F, const int* __restrict__ slots, int m,
-                                     const double* __restrict__ f, double c, long long n, double* __restrict__ part) {
+template <typename T>
+__global__ void anderson_gram_kernel(const T* __restrict__ F, const int* __restrict__ slots, int m,
+                                     const T* __restrict__ f, T c, long long n, double* __restrict__ part) {
     constexpr int MM = 16;
     const int nd = m * (m + 1) / 2 + m + 1;
-    double acc[MM * (MM + 1) / 2 + MM + 1];
-    for (int k = 0; k < nd; ++k) acc[k] = 0.0;
+    T acc[MM * (MM + 1) / 2 + MM + 1];   // per-thread partial sums over ~n/(grid) points
+    for (int k = 0; k < nd; ++k) acc[k] = T(0);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double v[MM];
+        T v[MM];
         for (int j = 0; j < m; ++j) v[j] = F[(long long)slots[j] * n + i];
-        const double fi = c * f[i];
+        const T fi = c * f[i];
         int k = 0;
         for (int a = 0; a < m; ++a)
             for (int b = a; b < m; ++b) acc[k++] += v[a] * v[b];
@@ -243,7 +243,7 @@ __global__ void anderson_gram_kernel(const double* __restrict__ F, const int* __
     __shared__ double sh[RB / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < nd; ++k) {
-        double v = acc[k];
+        double v = (double)acc[k];
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
         if (lane == 0) sh[warp] = v;
         __syncthreads();
@@ -602,7 +602,7 @@ void build_pseudocharge_and_sad(sdft_ctx* c) {
     double s = 0.0;
     dots_host(c, 1, a, b, c->ng, &s);
     const double scale = c->nelec / (c->dV * s);
-    axpby_kernel<<<nblocks(c->ng), 256, 0, c->stream>>>(c->rho_sad, c->rho_sad, 0.0, scale, c->ng);
+    axpby_kernel<double><<<nblocks(c->ng), 256, 0, c->stream>>>(c->rho_sad, c->rho_sad, 0.0, scale, c->ng);
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);
 }
@@ -626,6 +626,62 @@ void veff_assemble(sdft_ctx* c) {
 void veff_to_float(sdft_ctx* c, int spin) {
     const long long n = c->ng;
     to_float_grid_kernel<<<nblocks(n), 256, 0, c->stream>>>(c->veff + spin * n, c->veff32 + spin * n, n);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+// ---------------------------------------------------------------------------------------
+// Single-vector Laplacian step for the Poisson solver: out = -2 alpha (-1/2 L x) - beta b, i.e.
+// with alpha = -2, beta = -1:  out = b + L x (the residual of -L x = b).  One thread per grid
+// point with direct neighbour loads: the vector is a few MB and stays in L2, so a flat grid of
+// short independent threads beats the z-marching tile kernel built for orbital blocks.
+// ---------------------------------------------------------------------------------------
+struct LapCoef {
+    double c[3][FD_RADIUS + 1];  // -1/2 w_r / h_d^2
+    double c0;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) laplacian_residual_kernel(const T* __restrict__ x, const T* __restrict__ b,
+                                                                 T* __restrict__ out, LapCoef K, int n1, int n2,
+                                                                 int n3) {
+    const long long ng = (long long)n1 * n2 * n3;
+    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    const int i = (int)(g % n1);
+    const int j = (int)((g / n1) % n2);
+    const int k = (int)(g / ((long long)n1 * n2));
+    const long long plane = (long long)n1 * n2;
+    T acc = (T)K.c0 * x[g];
+#pragma unroll
+    for (int r = 1; r <= FD_RADIUS; ++r) {
+        int ip = i + r, im = i - r, jp = j + r, jm = j - r, kp = k + r, km = k - r;
+        ip -= ip >= n1 ? n1 : 0;
+        im += im < 0 ? n1 : 0;
+        jp -= jp >= n2 ? n2 : 0;
+        jm += jm < 0 ? n2 : 0;
+        kp -= kp >= n3 ? n3 : 0;
+        km += km < 0 ? n3 : 0;
+        const long long row = g - i, col = g - (long long)j * n1, pl = g - k * plane;
+        acc += (T)K.c[0][r] * (x[row + ip] + x[row + im]);
+        acc += (T)K.c[1][r] * (x[col + (long long)jp * n1] + x[col + (long long)jm * n1]);
+        acc += (T)K.c[2][r] * (x[pl + kp * plane] + x[pl + km * plane]);
+    }
+    // -L x = 2 * (-1/2 L x): out = b + L x = b - 2 acc
+    out[g] = b[g] - (T)2 * acc;
+}
+
+template <typename T>
+void laplacian_residual(sdft_ctx* c, const T* x, const T* b, T* out) {
+    LapCoef K;
+    for (int r = 0; r <= FD_RADIUS; ++r) {
+        K.c[0][r] = c->coef.cx[r];
+        K.c[1][r] = c->coef.cy[r];
+        K.c[2][r] = c->coef.cz[r];
+    }
+    K.c0 = c->coef.c0;
+    laplacian_residual_kernel<T><<<(unsigned)((c->ng + 255) / 256), 256, 0, c->stream>>>(x, b, out, K, c->n[0],
+                                                                                        c->n[1], c->n[2]);
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);
 }
@@ -668,7 +724,7 @@ int poisson_aar(sdft_ctx* c, const double* f, double* phi, double tol, int max_i
         SDFT_CUDA(cudaMemcpyAsync(c->scal, c->hscal, 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         add_scalar_kernel<<<nblocks(n), 256, 0, c->stream>>>(rhs, c->scal, 1.0, n);
         add_scalar_kernel<<<nblocks(n), 256, 0, c->stream>>>(phi, c->scal + 1, 1.0, n);
-        axpby_kernel<<<nblocks(n), 256, 0, c->stream>>>(rhs, rhs, 0.0, 4.0 * M_PI, n);
+        axpby_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(rhs, rhs, 0.0, 4.0 * M_PI, n);
         SDFT_CUDA(cudaGetLastError());
         count_launch(c, 5);
     }
@@ -687,10 +743,10 @@ int poisson_aar(sdft_ctx* c, const double* f, double* phi, double tol, int max_i
     int hslots[16];
     for (it = 0; it < max_iter; ++it) {
         // r = rhs - A phi = rhs + L phi  (stencil: alpha=-2 on -1/2 L, beta=-1 on rhs)
-        launch_cheb_step<double>(c, 0, phi, rhs, r, 1, nullptr, nullptr, -2.0, -1.0, 0.0);
+        laplacian_residual<double>(c, phi, rhs, r);
         // history push with f = cj * r
         const int slot = head;
-        anderson_push_kernel<<<nblocks(n), 256, 0, c->stream>>>(phi, r, cj, xprev, fprev, Xs + (long long)slot * n,
+        anderson_push_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(phi, r, cj, xprev, fprev, Xs + (long long)slot * n,
                                                                 Fs + (long long)slot * n, it > 0, n);
         count_launch(c);
         if (it > 0) {
@@ -703,9 +759,9 @@ int poisson_aar(sdft_ctx* c, const double* f, double* phi, double tol, int max_i
             std::memcpy(c->hscal + 512, hslots, sizeof(int) * 16);
             SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 512, sizeof(int) * count, cudaMemcpyHostToDevice, c->stream));
             const int nblk = 64;
-            anderson_gram_kernel<<<nblk, RB, 0, c->stream>>>(Fs, slots, count, r, cj, n, part);
+            anderson_gram_kernel<double><<<nblk, RB, 0, c->stream>>>(Fs, slots, count, r, cj, n, part);
             anderson_solve_kernel<<<1, 32, 0, c->stream>>>(part, nblk, count, gam, ffv);
-            anderson_update_kernel<<<nblocks(n), 256, 0, c->stream>>>(phi, r, cj, beta, Xs, Fs, slots, gam, count, n);
+            anderson_update_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(phi, r, cj, beta, Xs, Fs, slots, gam, count, n);
             SDFT_CUDA(cudaGetLastError());
             count_launch(c, 3);
             // convergence: ||r||^2 = ffv / cj^2
@@ -719,13 +775,168 @@ int poisson_aar(sdft_ctx* c, const double* f, double* phi, double tol, int max_i
             }
         } else {
             // Richardson: phi += omega * cj * r
-            axpby_kernel<<<nblocks(n), 256, 0, c->stream>>>(phi, r, omega * cj, 1.0, n);
+            axpby_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(phi, r, omega * cj, 1.0, n);
             SDFT_CUDA(cudaGetLastError());
             count_launch(c);
         }
     }
     if (it >= max_iter) return -it;
     return it;
+}
+
+// ---------------------------------------------------------------------------------------
+// Mixed-precision Poisson: FP64 residuals with FP32 AAR correction solves (iterative refinement).
+//   r = rhs + L phi (FP64);  A delta = r solved approximately in FP32 by AAR;  phi += delta.
+// Each refinement gains ~4-5 digits, so FP64-level residuals cost a few FP32 solves.
+// ---------------------------------------------------------------------------------------
+static int aar_fp32(sdft_ctx* c, const float* b, float* x, double tol_rel, int max_iter, double* final_rel) {
+    const long long n = c->ng;
+    const float omega = 0.6f, beta = 0.6f;
+    const int m = 7, p = 6;
+    float* r = c->work32 + 1 * n;
+    float* xprev = c->work32 + 2 * n;
+    float* fprev = c->work32 + 3 * n;
+    float* Xs = c->work32 + 4 * n;
+    float* Fs = Xs + (long long)m * n;
+    double* gam = c->scal + 64;
+    int* slots = (int*)(c->scal + 96);
+    double* ffv = c->scal + 128;
+    double* part = c->scal + 4096;
+    const float cj = (float)(1.0 / (2.0 * c->coef.c0));
+    double bnorm2;
+    {
+        // ||b||^2 through the history Gram with m = 0 (its last entry is (c f).(c f))
+        anderson_gram_kernel<float><<<64, RB, 0, c->stream>>>(Fs, slots, 0, b, 1.0f, n, part);
+        anderson_solve_kernel<<<1, 32, 0, c->stream>>>(part, 64, 0, gam, ffv);
+        count_launch(c, 2);
+        SDFT_CUDA(cudaMemcpyAsync(c->hscal, ffv, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+        bnorm2 = c->hscal[0];
+    }
+    SDFT_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * n, c->stream));
+    if (bnorm2 == 0.0) {
+        *final_rel = 0.0;
+        return 0;
+    }
+    int count = 0, head = 0, it = 0;
+    int hslots[16];
+    double rel = 1.0;
+    for (it = 0; it < max_iter; ++it) {
+        laplacian_residual<float>(c, x, b, r);
+        const int slot = head;
+        anderson_push_kernel<float><<<nblocks(n), 256, 0, c->stream>>>(x, r, cj, xprev, fprev, Xs + (long long)slot * n,
+                                                                       Fs + (long long)slot * n, it > 0, n);
+        count_launch(c);
+        if (it > 0) {
+            head = (head + 1) % m;
+            count = std::min(count + 1, m);
+        }
+        const bool anderson = ((it + 1) % p == 0) && count > 0;
+        if (anderson) {
+            for (int j = 0; j < count; ++j) hslots[j] = ((head - count + j) % m + m) % m;
+            std::memcpy(c->hscal + 512, hslots, sizeof(int) * 16);
+            SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 512, sizeof(int) * count, cudaMemcpyHostToDevice, c->stream));
+            const int nblk = 64;
+            anderson_gram_kernel<float><<<nblk, RB, 0, c->stream>>>(Fs, slots, count, r, cj, n, part);
+            anderson_solve_kernel<<<1, 32, 0, c->stream>>>(part, nblk, count, gam, ffv);
+            anderson_update_kernel<float><<<nblocks(n), 256, 0, c->stream>>>(x, r, cj, beta, Xs, Fs, slots, gam, count, n);
+            SDFT_CUDA(cudaGetLastError());
+            count_launch(c, 3);
+            SDFT_CUDA(cudaMemcpyAsync(c->hscal, ffv, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            SDFT_CUDA(cudaStreamSynchronize(c->stream));
+            rel = std::sqrt(c->hscal[0] / ((double)cj * cj) / bnorm2);
+            if (!std::isfinite(rel)) throw Error{SDFT_ERR_NONFINITE, "Poisson residual is not finite"};
+            if (rel <= tol_rel) {
+                ++it;
+                break;
+            }
+        } else {
+            axpby_kernel<float><<<nblocks(n), 256, 0, c->stream>>>(x, r, omega * cj, 1.0f, n);
+            SDFT_CUDA(cudaGetLastError());
+            count_launch(c);
+        }
+    }
+    *final_rel = rel;
+    return it;
+}
+
+int poisson_mixed(sdft_ctx* c, const double* f, double* phi, double tol, int max_iter) {
+    const long long n = c->ng;
+    ScopedTimer timer(c, SDFT_K_POISSON);
+    double* rhs = c->work64 + 0 * n;
+    double* r = c->work64 + 1 * n;
+    double* ones = c->work64 + 3 * n;
+    float* b32 = c->work32;
+    float* d32 = c->work32 + 18 * n;
+    // rhs = 4 pi (f - mean f); phi -= mean(phi)
+    SDFT_CUDA(cudaMemsetAsync(ones, 0, sizeof(double) * n, c->stream));
+    c->hscal[0] = 1.0;
+    SDFT_CUDA(cudaMemcpyAsync(c->scal, c->hscal, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    add_scalar_kernel<<<nblocks(n), 256, 0, c->stream>>>(ones, c->scal, 1.0, n);
+    {
+        const double* A[2] = {f, phi};
+        const double* B[2] = {ones, ones};
+        double s[2];
+        dots_host(c, 2, A, B, n, s);
+        SDFT_CUDA(cudaMemcpyAsync(rhs, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        c->hscal[0] = -s[0] / n;
+        c->hscal[1] = -s[1] / n;
+        SDFT_CUDA(cudaMemcpyAsync(c->scal, c->hscal, 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        add_scalar_kernel<<<nblocks(n), 256, 0, c->stream>>>(rhs, c->scal, 1.0, n);
+        add_scalar_kernel<<<nblocks(n), 256, 0, c->stream>>>(phi, c->scal + 1, 1.0, n);
+        axpby_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(rhs, rhs, 0.0, 4.0 * M_PI, n);
+        SDFT_CUDA(cudaGetLastError());
+        count_launch(c, 4);
+    }
+    double bnorm2;
+    {
+        const double* A[1] = {rhs};
+        dots_host(c, 1, A, A, n, &bnorm2);
+    }
+    if (bnorm2 == 0.0) {
+        SDFT_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * n, c->stream));
+        return 0;
+    }
+    // zero-mean gauge: FP32 corrections drift along the constant null vector of L, which the
+    // residual cannot see, so the mean is removed from phi at the end
+    auto remove_mean = [&]() {
+        const double* A[1] = {phi};
+        const double* B[1] = {ones};
+        double sphi;
+        dots_host(c, 1, A, B, n, &sphi);
+        c->hscal[0] = -sphi / n;
+        SDFT_CUDA(cudaMemcpyAsync(c->scal, c->hscal, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        add_scalar_kernel<<<nblocks(n), 256, 0, c->stream>>>(phi, c->scal, 1.0, n);
+        count_launch(c);
+    };
+    int total = 0;
+    for (int refine = 0; refine < 16; ++refine) {
+        // FP64 residual r = rhs + L phi
+        laplacian_residual<double>(c, phi, rhs, r);
+        double rn2;
+        {
+            const double* A[1] = {r};
+            dots_host(c, 1, A, A, n, &rn2);
+        }
+        const double rel = std::sqrt(rn2 / bnorm2);
+        if (!std::isfinite(rel)) throw Error{SDFT_ERR_NONFINITE, "Poisson residual is not finite"};
+        if (rel <= tol) {
+            remove_mean();
+            return std::max(total, 1);
+        }
+        if (total >= max_iter) break;
+        // FP32 correction A d = r: a relative reduction of 1e-3 per refinement stays above the
+        // FP32 rounding floor of the residual (~ cond(L) * 2^-24)
+        convert_add_kernel<float, double><<<nblocks(n), 256, 0, c->stream>>>(b32, r, 1.0, 0.0, n);
+        count_launch(c);
+        double inner_rel = 1.0;
+        const double want = std::max(1e-3, 0.3 * tol / rel);
+        total += aar_fp32(c, b32, d32, want, std::min(400, max_iter - total), &inner_rel);
+        convert_add_kernel<double, float><<<nblocks(n), 256, 0, c->stream>>>(phi, d32, 1.0, 1.0, n);
+        count_launch(c);
+    }
+    remove_mean();
+    return -std::max(total, 1);
 }
 
 void density_accumulate(sdft_ctx* c, int precision, bool cplx, const void* X, const double* occ, int ncol,
@@ -763,10 +974,10 @@ void pulay_update(sdft_ctx* c) {
     double* f = c->work64;  // needs nspin*ng <= 2 ng: use work64[0 .. 2ng)
     // f = rho_out - rho_in
     SDFT_CUDA(cudaMemcpyAsync(f, c->rho_out, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
-    axpby_kernel<<<nblocks(n), 256, 0, c->stream>>>(f, c->rho_in, -1.0, 1.0, n);
+    axpby_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(f, c->rho_in, -1.0, 1.0, n);
     count_launch(c);
     const int slot = c->mix_head;
-    anderson_push_kernel<<<nblocks(n), 256, 0, c->stream>>>(c->rho_in, f, 1.0, c->mix_xprev, c->mix_fprev,
+    anderson_push_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(c->rho_in, f, 1.0, c->mix_xprev, c->mix_fprev,
                                                             c->mix_dx + (long long)slot * n,
                                                             c->mix_df + (long long)slot * n, c->mix_k > 0, n);
     count_launch(c);
@@ -786,16 +997,16 @@ void pulay_update(sdft_ctx* c) {
         std::memcpy(c->hscal + 640, hslots, sizeof(int) * 16);
         SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 640, sizeof(int) * cnt, cudaMemcpyHostToDevice, c->stream));
         const int nblk = 32;  // 32 x (m(m+1)/2 + m + 1) <= 12288 partials for m <= 16
-        anderson_gram_kernel<<<nblk, RB, 0, c->stream>>>(c->mix_df, slots, cnt, f, 1.0, n, part);
+        anderson_gram_kernel<double><<<nblk, RB, 0, c->stream>>>(c->mix_df, slots, cnt, f, 1.0, n, part);
         anderson_solve_kernel<<<1, 32, 0, c->stream>>>(part, nblk, cnt, gam, ffv);
-        anderson_update_kernel<<<nblocks(n), 256, 0, c->stream>>>(c->rho_in, f, 1.0, c->opt.mix_beta, c->mix_dx,
+        anderson_update_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(c->rho_in, f, 1.0, c->opt.mix_beta, c->mix_dx,
                                                                   c->mix_df, slots, gam, cnt, n);
         count_launch(c, 3);
         if (c->opt.pulay_restart) {
             c->mix_count = 0;
         }
     } else {
-        axpby_kernel<<<nblocks(n), 256, 0, c->stream>>>(c->rho_in, f, c->opt.mix_beta, 1.0, n);
+        axpby_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(c->rho_in, f, c->opt.mix_beta, 1.0, n);
         count_launch(c);
     }
     SDFT_CUDA(cudaGetLastError());

@@ -45,6 +45,7 @@ struct Error {
 template <typename E> struct Elem;
 template <> struct Elem<float2> { using S = float; static constexpr int lanes = 2; };
 template <> struct Elem<double> { using S = double; static constexpr int lanes = 1; };
+template <> struct Elem<float> { using S = float; static constexpr int lanes = 1; };  // Poisson FP32 correction
 template <> struct Elem<double2> { using S = double; static constexpr int lanes = 2; };
 
 struct StencilCoef {
@@ -130,6 +131,7 @@ struct sdft_ctx {
     float* veff32 = nullptr;      // [nspin][ng]
     double* exc = nullptr;        // eps_xc
     double* work64 = nullptr;     // [28*ng] grid scratch (Poisson, mixing, energies, Lanczos)
+    float* work32 = nullptr;      // [20*ng] FP32 scratch of the mixed-precision Poisson solver
     // small device scalars / reductions [SCAL_DOUBLES], regions:
     //   [0,8) temporaries  [8,16) Fermi (mu, -TS, band energy)  [64,256) Anderson/Pulay small data
     //   [256,512) k-weights  [1024,1040) dot pointer tables  [1536,1544) dot results
@@ -208,6 +210,10 @@ template <typename E>
 void launch_cheb_step(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, int ncolE,
                       const typename Elem<E>::S* V, const E* kbC, double alpha, double beta,
                       double shift, bool with_kinetic = true);
+template <>
+void launch_cheb_step<float>(sdft_ctx* c, int kpt, const float* Y, const float* Yprev, float* Ynext, int ncolE,
+                             const float* V, const float* kbC, double alpha, double beta, double shift,
+                             bool with_kinetic);
 // KB projection C[col][a] = gamma_a * sum_j conj(beta_a(j)) Y[j, col]
 template <typename E>
 void launch_kb_project(sdft_ctx* c, int kpt, const E* Y, E* C, int ncolE);
@@ -222,6 +228,8 @@ void veff_assemble(sdft_ctx* c);
 void veff_to_float(sdft_ctx* c, int spin);
 void axpby_dev(sdft_ctx* c, double* y, const double* x, double a, double b, long long n);
 int poisson_aar(sdft_ctx* c, const double* f, double* phi, double tol, int max_iter);
+// same problem, FP64 residuals + FP32 AAR corrections; returns inner iterations (negative: failed)
+int poisson_mixed(sdft_ctx* c, const double* f, double* phi, double tol, int max_iter);
 // reductions: out[i] = sum_g a_i[g] * b_i[g] (device scal), returned synchronously to host
 void dots_host(sdft_ctx* c, int count, const double* const* a, const double* const* b, long long n,
                double* host_out);

@@ -393,8 +393,11 @@ sdft_status run_scf(sdft_ctx* c, sdft_result* out) {
         sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_in, nsp, c->b, ftmp, ng);
         count_launch(c);
         // the potential only needs to be as accurate as the current SCF error allows
-        const double ptol = std::max(c->opt.poisson_tol, std::min(1e-6, 1e-2 * last_err));
-        const int pit = poisson_aar(c, ftmp, c->phi, ptol, 4000);
+        // (and always an order of magnitude below the SCF target itself)
+        const double pfloor = std::min(c->opt.poisson_tol, 1e-2 * c->opt.scf_tol);
+        const double ptol = std::max(pfloor, std::min(1e-6, 1e-2 * last_err));
+        const int pit = prec == SDFT_MIXED ? poisson_mixed(c, ftmp, c->phi, ptol, 4000)
+                                           : poisson_aar(c, ftmp, c->phi, ptol, 4000);
         if (pit < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Poisson AAR did not converge"};
         veff_assemble(c);
         SDFT_CUDA(cudaStreamSynchronize(c->stream));
@@ -473,7 +476,9 @@ sdft_status run_scf(sdft_ctx* c, sdft_result* out) {
         SDFT_CUDA(cudaMemcpyAsync(phi_o, c->phi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, c->stream));
         sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_out, nsp, c->b, ftmp, ng);
         count_launch(c);
-        const int pit = poisson_aar(c, ftmp, phi_o, c->opt.poisson_tol, 2000);
+        const double ptol_o = std::min(c->opt.poisson_tol, 1e-2 * c->opt.scf_tol);
+        const int pit = prec == SDFT_MIXED ? poisson_mixed(c, ftmp, phi_o, ptol_o, 4000)
+                                           : poisson_aar(c, ftmp, phi_o, ptol_o, 4000);
         if (pit < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Poisson AAR did not converge"};
         double* vxc_o = c->work64 + 25 * ng;  // [nspin][ng]
         lda_device(c, nsp, c->rho_out, exc_o, vxc_o, (size_t)ng);

@@ -26,6 +26,15 @@ void launch_cheb_step<float2>(sdft_ctx* c, int kpt, const float2* Y, const float
     table[choice](c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, with_kinetic, true);
 }
 
+// scalar FP32, Laplacian-only: the correction solves of the mixed-precision Poisson solver
+template <>
+void launch_cheb_step<float>(sdft_ctx* c, int kpt, const float* Y, const float* Yprev, float* Ynext, int ncolE,
+                             const float* V, const float* kbC, double alpha, double beta, double shift,
+                             bool with_kinetic) {
+    launch_variant<float, false, 32, 8, 2, 2, 3>(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift,
+                                                 with_kinetic, true);
+}
+
 template <>
 void launch_kb_project<float2>(sdft_ctx* c, int kpt, const float2* Y, float2* C, int ncolE) {
     launch_project_impl<float2>(c, kpt, Y, C, ncolE);

@@ -39,26 +39,19 @@ __device__ __forceinline__ float2 eadd(float2 a, float2 b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
     return u2f(r);
 }
-// lane-wise a * b + acc
-__device__ __forceinline__ float2 efma2(float2 a, float2 b, float2 acc) {
-    unsigned long long r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(acc)));
-    return u2f(r);
-}
 __device__ __forceinline__ double efma(double s, double a, double acc) { return fma(s, a, acc); }
+__device__ __forceinline__ float efma(float s, float a, float acc) { return fmaf(s, a, acc); }
+__device__ __forceinline__ float eadd(float a, float b) { return a + b; }
 __device__ __forceinline__ double eadd(double a, double b) { return a + b; }
-__device__ __forceinline__ double efma2(double a, double b, double acc) { return fma(a, b, acc); }
 __device__ __forceinline__ double2 efma(double s, double2 a, double2 acc) {
     return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y));
 }
 __device__ __forceinline__ double2 eadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 efma2(double2 a, double2 b, double2 acc) {
-    return make_double2(fma(a.x, b.x, acc.x), fma(a.y, b.y, acc.y));
-}
 
 template <typename E> __device__ __forceinline__ E ezero();
 template <> __device__ __forceinline__ float2 ezero<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double ezero<double>() { return 0.0; }
+template <> __device__ __forceinline__ float ezero<float>() { return 0.f; }
 template <> __device__ __forceinline__ double2 ezero<double2>() { return make_double2(0.0, 0.0); }
 
 // complex multiply (for CPLX element types): a * b
@@ -129,6 +122,7 @@ struct ColRef {
 template <typename E> __device__ __forceinline__ E eone();
 template <> __device__ __forceinline__ float2 eone<float2>() { return make_float2(1.f, 0.f); }
 template <> __device__ __forceinline__ double eone<double>() { return 1.0; }
+template <> __device__ __forceinline__ float eone<float>() { return 1.f; }
 template <> __device__ __forceinline__ double2 eone<double2>() { return make_double2(1.0, 0.0); }
 
 template <typename E, typename S, bool CPLX>
@@ -509,10 +503,11 @@ void launch_variant(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, 
         else if (prev && !haskb) SDFT_STEP(true, false, true, true);
         else SDFT_STEP(false, false, true, true);
     } else {
-        // Laplacian-only form used by the Poisson solver (FP64 real, single vector)
+        // Laplacian-only form used by the Poisson solver (real, single vector, FP64 or FP32)
         SDFT_REQUIRE(prev && !haskb, SDFT_ERR_INVALID_ARG, "stencil variant without V_eff needs Yprev and no KB");
-        if constexpr (std::is_same<E, double>::value) SDFT_STEP(true, false, false, true);
-        else SDFT_REQUIRE(false, SDFT_ERR_INVALID_ARG, "Laplacian-only stencil is FP64 real only");
+        if constexpr (std::is_same<E, double>::value || std::is_same<E, float>::value)
+            SDFT_STEP(true, false, false, true);
+        else SDFT_REQUIRE(false, SDFT_ERR_INVALID_ARG, "Laplacian-only stencil is real only");
     }
 #undef SDFT_STEP
     SDFT_CUDA(cudaGetLastError());

@@ -186,6 +186,19 @@ def test_poisson_aar_matches_exact_solve(sd):
     assert _relerr(phi.cpu().numpy(), ref) < 1e-9
 
 
+def test_poisson_mixed_refinement_matches_exact_solve(sd):
+    # FP32 AAR corrections inside FP64 residual refinement still reach FP64-level accuracy
+    cell = workloads.two_atom_cell()
+    ctx = _ctx(sd, cell, sd.SDFT_MIXED, 8)
+    f = model.sad_density(cell) + model.pseudocharge(cell)
+    ref = ham.poisson_exact(cell, f)
+    ft = torch.from_numpy(f).cuda()
+    phi = torch.zeros_like(ft)
+    it = sd.sdft_poisson(ctx, ft, phi, 1e-11, 4000)
+    assert it > 0
+    assert _relerr(phi.cpu().numpy(), ref) < 1e-9
+
+
 @pytest.mark.parametrize("nspin", [1, 2])
 def test_lda_matches_oracle(sd, nspin):
     cell = workloads.two_atom_cell()
