@@ -371,6 +371,10 @@ void subspace_gram_noalloc(int precision, bool cplx, const void* Y, const void* 
 
 void subspace_gram(sdft_ctx* c, int precision, bool cplx, const void* Y, const void* HY, double* M, double* Hs,
                    int ncol) {
+    if (gram_tc_supported(precision, cplx, ncol)) {
+        subspace_gram_tc(c, Y, HY, M, Hs, ncol);
+        return;
+    }
     const int kind = kind_of(precision, cplx);
     const int tiles = (ncol + GT - 1) / GT;
     const int w = cplx ? 2 : 1;

@@ -1,0 +1,340 @@
+// Subspace Gram matrices of Rayleigh-Ritz on the 5th-generation tensor cores (paper Sec. 2.1
+// CheFSI; Sec. 4 names the subspace work as the step that dominates at scale):
+//   M = Y^T Y,  Hs = Y^T (H Y)   for FP32 orbital blocks (paired layout), ncol up to ~1000,
+// as BF16x3 split products  a*b ~ hi(a)hi(b) + hi(a)lo(b) + lo(a)hi(b),  hi = bf16(a),
+// lo = bf16(a - hi), accumulated in FP32 in tensor memory (TMEM).
+//
+// One CTA = one 128 x 128 tile pair (i, j >= i) of the output and one split of the grid (the
+// contraction index, up to ~1.7 M points).  All 256 threads stream FP32 Y / HY from HBM, split
+// every value into bf16 hi and lo and store them into K-major, 128-byte-swizzled shared-memory
+// tiles (two stages); thread 0 issues tcgen05.mma (M=128, N=128, K=16) for both products and
+// tracks completion with tcgen05.commit on an mbarrier.  The epilogue reads the two FP32
+// accumulators with tcgen05.ld and writes per-split partial tiles that a second kernel sums in
+// FP64.  Every mbarrier wait is bounded: on timeout the kernel sets an error flag and returns.
+#include "internal.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <vector>
+
+namespace sdft {
+namespace {
+
+constexpr int TC_M = 128;          // rows of a tile (orbitals i)
+constexpr int TC_N = 128;          // columns of a tile (orbitals j)
+constexpr int TC_K = 64;           // grid points per stage (one 128-byte swizzle row of bf16)
+constexpr int TILE_BYTES = TC_M * TC_K * 2;  // one bf16 operand tile: 16 KB
+constexpr int NSTAGE = 2;
+// per stage: A hi/lo, B hi/lo (Y_j), C hi/lo (HY_j)
+constexpr int STAGE_BYTES = 6 * TILE_BYTES;
+constexpr long long WAIT_LIMIT = 1LL << 26;  // try_wait polls before giving up
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ---- tcgen05 wrappers ------------------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_before_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// 32 lanes x 32 bit, 8 consecutive columns per thread
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, K-major tile with 128-byte swizzle: 8-row groups of 1024 B
+// (stride byte offset 1024), descriptor version 1, layout type SWIZZLE_128B (2).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(1) << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // SWIZZLE_128B
+    return d;
+}
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// byte offset of element (r, k) of a [rows x 64] bf16 K-major SW128 tile
+__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Load the [128 rows x 64 points] FP32 tile (rows = orbitals row0.., paired layout) starting at
+// grid point g0, split into bf16 hi/lo and store into the two swizzled tiles.  Rows >= ncol and
+// points >= g1 are zero.  Each work item = one orbital pair x 8 consecutive points (16-byte chunk
+// per row and part).
+__device__ __forceinline__ void stage_tile(const float* __restrict__ Y, long long ng, int ncol, int row0,
+                                           long long g0, long long g1, unsigned char* hi_tile,
+                                           unsigned char* lo_tile) {
+    for (int item = threadIdx.x; item < (TC_M / 2) * (TC_K / 8); item += blockDim.x) {
+        const int pr = item / (TC_K / 8);          // pair within the tile
+        const int ch = item - pr * (TC_K / 8);     // 8-point chunk
+        const int r0 = 2 * pr;                     // rows r0, r0+1 = orbitals row0+r0, +1
+        const int orb = row0 + r0;
+        __align__(16) __nv_bfloat16 h0[8], l0[8], h1[8], l1[8];
+        const long long gs = g0 + ch * 8;
+        if (orb < ncol) {
+            const float2* src = reinterpret_cast<const float2*>(Y) + ((long long)(orb >> 1) * ng + gs);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                float2 v = make_float2(0.f, 0.f);
+                if (gs + e < g1) v = __ldg(src + e);
+                split_bf16(v.x, h0[e], l0[e]);
+                split_bf16(v.y, h1[e], l1[e]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) h0[e] = l0[e] = h1[e] = l1[e] = __float2bfloat16_rn(0.f);
+        }
+        *reinterpret_cast<uint4*>(hi_tile + sw128_off(r0, ch * 8)) = *reinterpret_cast<uint4*>(h0);
+        *reinterpret_cast<uint4*>(lo_tile + sw128_off(r0, ch * 8)) = *reinterpret_cast<uint4*>(l0);
+        *reinterpret_cast<uint4*>(hi_tile + sw128_off(r0 + 1, ch * 8)) = *reinterpret_cast<uint4*>(h1);
+        *reinterpret_cast<uint4*>(lo_tile + sw128_off(r0 + 1, ch * 8)) = *reinterpret_cast<uint4*>(l1);
+    }
+}
+
+struct TilePair {
+    int ti, tj;
+};
+
+// grid: (tile pairs, splits); 256 threads; dynamic smem NSTAGE * STAGE_BYTES + 2 KB
+__global__ void __launch_bounds__(256, 1)
+gram_tc_kernel(const float* __restrict__ Y, const float* __restrict__ HY, int ncol, long long ng, long long chunk,
+               const TilePair* __restrict__ pairs, float* __restrict__ part, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);   // one per stage
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NSTAGE);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const TilePair tp = pairs[blockIdx.x];
+    const bool diag = tp.ti == tp.tj;
+    const int row_i = tp.ti * TC_M, row_j = tp.tj * TC_N;
+    const long long g0 = blockIdx.y * chunk;
+    const long long g1 = min(ng, g0 + chunk);
+    const int ntile = (int)((g1 - g0 + TC_K - 1) / TC_K);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, 256);   // columns [0,128): M tile, [128,256): Hs tile
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+    bool ok = true;
+
+    for (int t = 0; t < ntile; ++t) {
+        const int s = t % NSTAGE;
+        unsigned char* st = smem + s * STAGE_BYTES;
+        unsigned char *a_hi = st, *a_lo = st + TILE_BYTES, *b_hi = st + 2 * TILE_BYTES, *b_lo = st + 3 * TILE_BYTES;
+        unsigned char *c_hi = st + 4 * TILE_BYTES, *c_lo = st + 5 * TILE_BYTES;
+        // the MMAs that read this stage two tiles ago must be complete before it is refilled
+        if (t >= NSTAGE) {
+            if (!mbar_wait(&bars[s], (uint32_t)(((t - NSTAGE) / NSTAGE) & 1))) {
+                ok = false;
+                break;
+            }
+        }
+        const long long gt = g0 + (long long)t * TC_K;
+        stage_tile(Y, ng, ncol, row_i, gt, g1, a_hi, a_lo);
+        if (!diag) stage_tile(Y, ng, ncol, row_j, gt, g1, b_hi, b_lo);
+        stage_tile(HY, ng, ncol, row_j, gt, g1, c_hi, c_lo);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            fence_after_sync();
+            const uint32_t ah = su32(a_hi), al = su32(a_lo);
+            const uint32_t bh = diag ? ah : su32(b_hi), bl = diag ? al : su32(b_lo);
+            const uint32_t ch = su32(c_hi), cl = su32(c_lo);
+#pragma unroll
+            for (int kk = 0; kk < TC_K / 16; ++kk) {
+                const uint32_t ko = kk * 32;  // 16 bf16 = 32 bytes along the swizzled row
+                const uint32_t acc0 = (t > 0 || kk > 0) ? 1u : 0u;
+                // M += Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T
+                mma_bf16(tmem, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, acc0);
+                mma_bf16(tmem, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
+                mma_bf16(tmem, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
+                // Hs += Ahi Chi^T + Ahi Clo^T + Alo Chi^T
+                mma_bf16(tmem + 128, sw128_desc(ah + ko), sw128_desc(ch + ko), idesc, acc0);
+                mma_bf16(tmem + 128, sw128_desc(ah + ko), sw128_desc(cl + ko), idesc, 1u);
+                mma_bf16(tmem + 128, sw128_desc(al + ko), sw128_desc(ch + ko), idesc, 1u);
+            }
+            mma_commit(&bars[s]);
+        }
+    }
+    // drain: wait for the last commit of every stage that was used
+    if (ok) {
+        for (int t = std::max(0, ntile - NSTAGE); t < ntile; ++t) {
+            const int s = t % NSTAGE;
+            if (!mbar_wait(&bars[s], (uint32_t)((t / NSTAGE) & 1))) ok = false;
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+    }
+    fence_after_sync();
+    __syncthreads();
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        // bounded second wait for MMAs still in flight before the tensor memory is released
+        for (int s = 0; s < NSTAGE; ++s)
+            for (int par = 0; par < 2; ++par) mbar_wait(&bars[s], par);
+        __syncthreads();
+        if (warp == 0) tmem_dealloc(tmem, 256);
+        return;
+    }
+    // epilogue: warps 0-3 read rows 32w..32w+31 of both accumulators (TMEM lanes = rows)
+    const long long nn = (long long)ncol * ncol;
+    float* pm = part + (long long)blockIdx.y * 2 * nn;
+    float* ph = pm + nn;
+    if (warp < 4 && ntile > 0) {
+        const int row = 32 * warp + lane;
+        const int gi = row_i + row;
+        for (int c0 = 0; c0 < TC_N; c0 += 8) {
+            float vm[8], vh[8];
+            const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+            tmem_ld8(tmem + lane_base + c0, vm);
+            tmem_ld8(tmem + lane_base + 128 + c0, vh);
+            if (gi < ncol) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int gj = row_j + c0 + e;
+                    if (gj < ncol && gj >= gi) {
+                        pm[(long long)gi + (long long)gj * ncol] = vm[e];
+                        ph[(long long)gi + (long long)gj * ncol] = vh[e];
+                    }
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// sum FP32 partials over splits in FP64 (upper triangle) and mirror
+__global__ void gram_tc_reduce_kernel(const float* __restrict__ part, int nsplit, int ncol, double* __restrict__ M,
+                                      double* __restrict__ Hs) {
+    const long long nn = (long long)ncol * ncol;
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < nn; o += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(o % ncol), j = (int)(o / ncol);
+        if (j < i) continue;
+        double m = 0.0, h = 0.0;
+        for (int s = 0; s < nsplit; ++s) {
+            m += (double)part[(long long)s * 2 * nn + o];
+            h += (double)part[(long long)s * 2 * nn + nn + o];
+        }
+        const long long ot = (long long)j + (long long)i * ncol;
+        M[o] = m;
+        M[ot] = m;
+        Hs[o] = h;
+        Hs[ot] = h;
+    }
+}
+
+}  // namespace
+
+bool gram_tc_supported(int precision, bool cplx, int ncol) {
+    return precision == SDFT_MIXED && !cplx && ncol >= 32 && ncol % 2 == 0 && getenv("SDFT_NO_TCGEN05") == nullptr;
+}
+
+void subspace_gram_tc(sdft_ctx* c, const void* Y, const void* HY, double* M, double* Hs, int ncol) {
+    const int tiles = (ncol + TC_M - 1) / TC_M;
+    std::vector<TilePair> hp;
+    for (int i = 0; i < tiles; ++i)
+        for (int j = i; j < tiles; ++j) hp.push_back(TilePair{i, j});
+    const int npair = (int)hp.size();
+    const long long nn = (long long)ncol * ncol;
+    // splits: about two CTAs per SM in total, bounded by the partial buffer (FP32, 2 nn per split)
+    long long nsplit = std::max<long long>(1, (2LL * 152) / npair);
+    nsplit = std::min<long long>(nsplit, (long long)(c->part_elems * 2 / (2 * nn)));
+    nsplit = std::max<long long>(1, std::min<long long>(nsplit, (c->ng + TC_K - 1) / TC_K));
+    long long chunk = (c->ng + nsplit - 1) / nsplit;
+    chunk = (chunk + TC_K - 1) / TC_K * TC_K;
+    nsplit = (c->ng + chunk - 1) / chunk;
+    SDFT_REQUIRE((size_t)(nsplit * 2 * nn) <= c->part_elems * 2, SDFT_ERR_INVALID_ARG, "gram_tc: partials");
+    TilePair* dpairs = reinterpret_cast<TilePair*>(c->scal + 512);   // <= 64 pairs fit in [512, 1024)
+    SDFT_REQUIRE(npair <= 64, SDFT_ERR_INVALID_ARG, "gram_tc: too many tiles");
+    SDFT_CUDA(cudaMemcpyAsync(dpairs, hp.data(), sizeof(TilePair) * npair, cudaMemcpyHostToDevice, c->stream));
+    int* derr = reinterpret_cast<int*>(c->scal + 4);
+    SDFT_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), c->stream));
+    const size_t dsm = NSTAGE * STAGE_BYTES + 1024 + 256;
+    SDFT_CUDA(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+    ScopedTimer timer(c, SDFT_K_GRAM, 0.0, 2.0 * (double)c->ng * ncol * ncol);
+    float* part = reinterpret_cast<float*>(c->part);
+    gram_tc_kernel<<<dim3(npair, (unsigned)nsplit), 256, dsm, c->stream>>>(
+        (const float*)Y, (const float*)HY, ncol, c->ng, chunk, dpairs, part, derr);
+    SDFT_CUDA(cudaGetLastError());
+    gram_tc_reduce_kernel<<<(unsigned)std::min<long long>((nn + 255) / 256, 2048), 256, 0, c->stream>>>(
+        part, (int)nsplit, ncol, M, Hs);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c, 2);
+    int herr = 0;
+    SDFT_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    if (herr) throw Error{SDFT_ERR_DEVICE_TIMEOUT, "tensor-core Gram: an mbarrier wait timed out"};
+}
+
+}  // namespace sdft

@@ -174,6 +174,31 @@ def test_subspace_matrices_and_rotation_mixed(sd):
     assert _relerr(sd.unpack_block(x, 1, False), ref) < 1e-5
 
 
+@pytest.mark.parametrize("n", [(9, 10, 11), (40, 40, 40)])
+def test_gram_tcgen05_bf16x3_matches_fp64(sd, n):
+    # 154 orbitals (two 128-row tiles, three tile pairs): the tensor-core BF16x3 path.  The split
+    # product drops lo*lo and the bf16 remainders: ~2^-16 relative per product, far less after
+    # summation; 2e-5 of sqrt(M_ii M_jj) is the bar.
+    cell = workloads.small_cell(npts=10, L=4.0, natom=2, seed=5, nstates=154)
+    cell.n = n
+    cell.L = tuple(0.4 * x for x in n)
+    ns = 154
+    ng = int(np.prod(n))
+    ctx = _ctx(sd, cell, sd.SDFT_MIXED, ns)
+    rng = np.random.default_rng(17)
+    Y = rng.normal(size=(ns, ng)).astype(np.float32).astype(np.float64)
+    HY = rng.normal(size=(ns, ng)).astype(np.float32).astype(np.float64)
+    m = torch.empty(ns, ns, dtype=torch.float64, device="cuda")
+    h = torch.empty_like(m)
+    sd.sdft_subspace_matrices(ctx, 0, sd.SDFT_MIXED, sd.pack_block(Y, 1), sd.pack_block(HY, 1), m, h, ns)
+    M_ref = Y @ Y.T
+    upper = np.triu(Y @ HY.T)
+    H_ref = upper + np.triu(upper, 1).T
+    scale = np.sqrt(np.outer(np.diag(M_ref), np.diag(M_ref)))
+    assert np.max(np.abs(m.cpu().numpy().T - M_ref) / scale) < 2e-5
+    assert np.max(np.abs(h.cpu().numpy().T - H_ref) / scale) < 2e-5
+
+
 def test_poisson_aar_matches_exact_solve(sd):
     cell = workloads.two_atom_cell()
     ctx = _ctx(sd, cell, sd.SDFT_FP64, 8)
