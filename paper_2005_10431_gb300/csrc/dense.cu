@@ -434,14 +434,18 @@ void generalized_eig(sdft_ctx* c, bool cplx, double* M, double* Hs, double* eig,
 void rotate_block(sdft_ctx* c, int precision, bool cplx, const void* Y, const double* Q, void* X, int ncol) {
     const int kind = kind_of(precision, cplx);
     dim3 grid((unsigned)((c->ng + 63) / 64), (ncol + 31) / 32);
-    ScopedTimer timer(c, SDFT_K_ROTATE, 0.0, 2.0 * (double)c->ng * ncol * ncol * (cplx ? 4.0 : 1.0));
     const void* Qp = Q;
     if (precision != SDFT_FP64) {
         const long long nq = (long long)ncol * ncol * (cplx ? 2 : 1);
         to_float_kernel<<<nb(nq), 256, 0, c->stream>>>(Q, (float*)c->Q32, nq);
         count_launch(c);
         Qp = c->Q32;
+        if (rotate_tc_supported(precision, cplx, ncol)) {
+            rotate_tc(c, Y, (const float*)c->Q32, X, ncol);
+            return;
+        }
     }
+    ScopedTimer timer(c, SDFT_K_ROTATE, 0.0, 2.0 * (double)c->ng * ncol * ncol * (cplx ? 4.0 : 1.0));
     switch (kind) {
         case 0: rotate_kernel<0><<<grid, 256, 0, c->stream>>>(Y, Qp, X, ncol, c->ng); break;
         case 1: rotate_kernel<1><<<grid, 256, 0, c->stream>>>(Y, Qp, X, ncol, c->ng); break;

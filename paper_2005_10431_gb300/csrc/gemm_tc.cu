@@ -294,6 +294,166 @@ __global__ void gram_tc_reduce_kernel(const float* __restrict__ part, int nsplit
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Rotation X = Y Q on the tensor cores (BF16x3, FP32 accumulation):
+//   D[128 grid points][128 orbitals j] = sum_k Y[g][k] Q[k][j]  (A = Y tile, B[j][k] = Q[k][j]).
+// The producer transposes the paired-layout Y tile into a K-major (orbital-contiguous) swizzled
+// tile; Q (FP64, column-major) is K-major as stored.  grid = (grid-point tiles, j tiles).
+// ---------------------------------------------------------------------------------------
+constexpr int ROT_STAGE_BYTES = 4 * TILE_BYTES;   // A hi/lo, B hi/lo
+
+// A tile: rows = grid points g0.. (128), k = orbitals k0..k0+63 of the paired layout.
+// Work item = one grid point x 16 consecutive orbitals (two 16-byte chunks per part).
+__device__ __forceinline__ void stage_rot_a(const float* __restrict__ Y, long long ng, int ncol, long long g0,
+                                            int k0, unsigned char* hi_tile, unsigned char* lo_tile) {
+    for (int item = threadIdx.x; item < TC_M * (TC_K / 16); item += blockDim.x) {
+        const int r = item % TC_M;           // consecutive threads: consecutive grid points
+        const int q = item / TC_M;           // 16-orbital group
+        const long long g = g0 + r;
+        __align__(16) __nv_bfloat16 h[16], l[16];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = k0 + 16 * q + 2 * e;          // orbital pair (k, k+1)
+            float2 v = make_float2(0.f, 0.f);
+            if (g < ng && k < ncol) v = __ldg(reinterpret_cast<const float2*>(Y) + ((long long)(k >> 1) * ng + g));
+            split_bf16(v.x, h[2 * e], l[2 * e]);
+            split_bf16(v.y, h[2 * e + 1], l[2 * e + 1]);
+        }
+        *reinterpret_cast<uint4*>(hi_tile + sw128_off(r, 16 * q)) = *reinterpret_cast<uint4*>(h);
+        *reinterpret_cast<uint4*>(hi_tile + sw128_off(r, 16 * q + 8)) = *reinterpret_cast<uint4*>(h + 8);
+        *reinterpret_cast<uint4*>(lo_tile + sw128_off(r, 16 * q)) = *reinterpret_cast<uint4*>(l);
+        *reinterpret_cast<uint4*>(lo_tile + sw128_off(r, 16 * q + 8)) = *reinterpret_cast<uint4*>(l + 8);
+    }
+}
+
+// B tile: rows = output orbitals j0.. (128), k = input orbitals k0..k0+63: B[j][k] = Q[k + j n]
+__device__ __forceinline__ void stage_rot_b(const float* __restrict__ Q32, int ncol, int j0, int k0,
+                                            unsigned char* hi_tile, unsigned char* lo_tile) {
+    for (int item = threadIdx.x; item < TC_N * (TC_K / 8); item += blockDim.x) {
+        const int r = item / (TC_K / 8);
+        const int ch = item - r * (TC_K / 8);
+        const int j = j0 + r;
+        __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = k0 + ch * 8 + e;
+            const float v = (j < ncol && k < ncol) ? Q32[(long long)k + (long long)j * ncol] : 0.f;
+            split_bf16(v, h[e], l[e]);
+        }
+        *reinterpret_cast<uint4*>(hi_tile + sw128_off(r, ch * 8)) = *reinterpret_cast<uint4*>(h);
+        *reinterpret_cast<uint4*>(lo_tile + sw128_off(r, ch * 8)) = *reinterpret_cast<uint4*>(l);
+    }
+}
+
+__global__ void __launch_bounds__(256, 1)
+rotate_tc_kernel(const float* __restrict__ Y, const float* __restrict__ Q32, float* __restrict__ X, int ncol,
+                 long long ng, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * ROT_STAGE_BYTES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NSTAGE);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long g0 = (long long)blockIdx.x * TC_M;
+    const int j0 = blockIdx.y * TC_N;
+    const int nk = (ncol + TC_K - 1) / TC_K;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, 128);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+    bool ok = true;
+    for (int t = 0; t < nk; ++t) {
+        const int s = t % NSTAGE;
+        unsigned char* st = smem + s * ROT_STAGE_BYTES;
+        unsigned char *a_hi = st, *a_lo = st + TILE_BYTES, *b_hi = st + 2 * TILE_BYTES, *b_lo = st + 3 * TILE_BYTES;
+        if (t >= NSTAGE) {
+            if (!mbar_wait(&bars[s], (uint32_t)(((t - NSTAGE) / NSTAGE) & 1))) {
+                ok = false;
+                break;
+            }
+        }
+        stage_rot_a(Y, ng, ncol, g0, t * TC_K, a_hi, a_lo);
+        stage_rot_b(Q32, ncol, j0, t * TC_K, b_hi, b_lo);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            fence_after_sync();
+            const uint32_t ah = su32(a_hi), al = su32(a_lo), bh = su32(b_hi), bl = su32(b_lo);
+#pragma unroll
+            for (int kk = 0; kk < TC_K / 16; ++kk) {
+                const uint32_t ko = kk * 32;
+                mma_bf16(tmem, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, (t > 0 || kk > 0) ? 1u : 0u);
+                mma_bf16(tmem, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
+                mma_bf16(tmem, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
+            }
+            mma_commit(&bars[s]);
+        }
+    }
+    if (ok) {
+        for (int t = std::max(0, nk - NSTAGE); t < nk; ++t) {
+            const int s = t % NSTAGE;
+            if (!mbar_wait(&bars[s], (uint32_t)((t / NSTAGE) & 1))) ok = false;
+        }
+    }
+    fence_after_sync();
+    __syncthreads();
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        for (int s = 0; s < NSTAGE; ++s)
+            for (int par = 0; par < 2; ++par) mbar_wait(&bars[s], par);
+        __syncthreads();
+        if (warp == 0) tmem_dealloc(tmem, 128);
+        return;
+    }
+    // epilogue: row = grid point, 8 orbitals per tcgen05.ld; store pairs into the paired layout
+    if (warp < 4) {
+        const long long g = g0 + 32 * warp + lane;
+        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        for (int c0 = 0; c0 < TC_N; c0 += 8) {
+            float v[8];
+            tmem_ld8(tmem + lane_base + c0, v);
+            if (g < ng) {
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    const int j = j0 + c0 + e;
+                    if (j < ncol)
+                        reinterpret_cast<float2*>(X)[(long long)(j >> 1) * ng + g] = make_float2(v[e], v[e + 1]);
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+}  // namespace
+
+bool rotate_tc_supported(int precision, bool cplx, int ncol) { return gram_tc_supported(precision, cplx, ncol); }
+
+// X = Y Q for FP32 paired blocks; Q32 is Q in FP32, column-major ncol x ncol
+void rotate_tc(sdft_ctx* c, const void* Y, const float* Q32, void* X, int ncol) {
+    int* derr = reinterpret_cast<int*>(c->scal + 5);
+    SDFT_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), c->stream));
+    const size_t dsm = NSTAGE * ROT_STAGE_BYTES + 1024 + 256;
+    SDFT_CUDA(cudaFuncSetAttribute(rotate_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+    dim3 grid((unsigned)((c->ng + TC_M - 1) / TC_M), (ncol + TC_N - 1) / TC_N);
+    ScopedTimer timer(c, SDFT_K_ROTATE, 0.0, 2.0 * (double)c->ng * ncol * ncol);
+    rotate_tc_kernel<<<grid, 256, dsm, c->stream>>>((const float*)Y, Q32, (float*)X, ncol, c->ng, derr);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+    int herr = 0;
+    SDFT_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    if (herr) throw Error{SDFT_ERR_DEVICE_TIMEOUT, "tensor-core rotation: an mbarrier wait timed out"};
+}
+
+namespace {
 }  // namespace
 
 bool gram_tc_supported(int precision, bool cplx, int ncol) {

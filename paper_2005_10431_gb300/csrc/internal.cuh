@@ -246,6 +246,8 @@ void subspace_gram(sdft_ctx* c, int precision, bool cplx, const void* Y, const v
 // tcgen05 BF16x3 path of subspace_gram for FP32 real blocks (gemm_tc.cu)
 bool gram_tc_supported(int precision, bool cplx, int ncol);
 void subspace_gram_tc(sdft_ctx* c, const void* Y, const void* HY, double* M, double* Hs, int ncol);
+bool rotate_tc_supported(int precision, bool cplx, int ncol);
+void rotate_tc(sdft_ctx* c, const void* Y, const float* Q32, void* X, int ncol);
 // allocation-free variant: partials in a fixed file-scope device array (no context needed)
 void subspace_gram_noalloc(int precision, bool cplx, const void* Y, const void* HY, long long ng, int ncol,
                            double* M, double* Hs, cudaStream_t stream);

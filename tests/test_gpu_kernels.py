@@ -199,6 +199,28 @@ def test_gram_tcgen05_bf16x3_matches_fp64(sd, n):
     assert np.max(np.abs(h.cpu().numpy().T - H_ref) / scale) < 2e-5
 
 
+@pytest.mark.parametrize("n", [(9, 10, 11), (40, 40, 40)])
+def test_rotation_tcgen05_bf16x3_matches_fp64(sd, n):
+    # X = Y Q with 154 orbitals on the tensor cores (two 128-column tiles, three K tiles, a
+    # ragged last grid tile): BF16x3 of FP32 operands, error ~2^-16 of |Y||Q| per term.
+    cell = workloads.small_cell(npts=10, L=4.0, natom=2, seed=5, nstates=154)
+    cell.n = n
+    cell.L = tuple(0.4 * x for x in n)
+    ns = 154
+    ng = int(np.prod(n))
+    ctx = _ctx(sd, cell, sd.SDFT_MIXED, ns)
+    rng = np.random.default_rng(23)
+    Y = rng.normal(size=(ns, ng)).astype(np.float32).astype(np.float64)
+    Q = np.linalg.qr(rng.normal(size=(ns, ns)))[0]
+    q = torch.from_numpy(np.ascontiguousarray(Q.T)).cuda()   # column-major Q
+    y = sd.pack_block(Y, 1)
+    x = torch.empty_like(y)
+    sd.sdft_rotate(ctx, 0, sd.SDFT_MIXED, y, q, x, ns)
+    ref = (Y.T @ Q.astype(np.float32).astype(np.float64)).T
+    err = np.abs(sd.unpack_block(x, 1, False) - ref)
+    assert np.max(err) < 2e-5 * np.max(np.abs(Y)) * np.sqrt(ns)
+
+
 def test_poisson_aar_matches_exact_solve(sd):
     cell = workloads.two_atom_cell()
     ctx = _ctx(sd, cell, sd.SDFT_FP64, 8)
