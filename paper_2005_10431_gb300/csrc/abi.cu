@@ -221,6 +221,8 @@ void build_context(sdft_ctx* c) {
     SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "sygvd workspace query failed");
     c->solver_lwork = std::max(c->solver_lwork, lw);
     if (const char* env = getenv("SDFT_EIGEN")) c->eig_method = atoi(env);
+    if (const char* env = getenv("SDFT_AAR_PERSISTENT")) c->aar_persistent = atoi(env) != 0;
+    if (const char* env = getenv("SDFT_TEST_BARRIER_EXTRA")) c->test_barrier_extra = atoi(env) != 0;
     cs = cusolverDnCreateSyevjInfo(&c->syevj_params);
     SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "syevj info");
     cusolverDnXsyevjSetTolerance(c->syevj_params, 1e-14);

@@ -222,53 +222,94 @@ __global__ void anderson_update_kernel(T* __restrict__ x, const T* __restrict__ 
     }
 }
 
-// Gram of the history: G[i][j] = F_i . F_j (i <= j), r_i = F_i . (c f), plus f.f; partials per block
-template <typename T>
-__global__ void anderson_gram_kernel(const T* __restrict__ F, const int* __restrict__ slots, int m,
-                                     const T* __restrict__ f, T c, long long n, double* __restrict__ part) {
-    constexpr int MM = 16;
-    const int nd = m * (m + 1) / 2 + m + 1;
-    T acc[MM * (MM + 1) / 2 + MM + 1];   // per-thread partial sums over ~n/(grid) points
-    for (int k = 0; k < nd; ++k) acc[k] = T(0);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        T v[MM];
-        for (int j = 0; j < m; ++j) v[j] = F[(long long)slots[j] * n + i];
+// Gram of the history: G[i][j] = F_i . F_j (i <= j), r_i = F_i . (c f), plus f.f, for points
+// [lo, hi) strided by `step`; C = history length at compile time keeps the accumulators in registers.
+template <int C, typename T>
+__device__ __forceinline__ void gram_accum(const T* __restrict__ F, const int* sl, const T* __restrict__ f, T c,
+                                           long long n, long long lo, long long hi, long long step, double* out) {
+    constexpr int ND = C * (C + 1) / 2 + C + 1;
+    T acc[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) acc[k] = T(0);
+    for (long long i = lo; i < hi; i += step) {
+        T v[C > 0 ? C : 1];
+#pragma unroll
+        for (int j = 0; j < C; ++j) v[j] = F[(long long)sl[j] * n + i];
         const T fi = c * f[i];
         int k = 0;
-        for (int a = 0; a < m; ++a)
-            for (int b = a; b < m; ++b) acc[k++] += v[a] * v[b];
-        for (int a = 0; a < m; ++a) acc[k++] += v[a] * fi;
+#pragma unroll
+        for (int a = 0; a < C; ++a)
+#pragma unroll
+            for (int b = a; b < C; ++b) acc[k++] += v[a] * v[b];
+#pragma unroll
+        for (int a = 0; a < C; ++a) acc[k++] += v[a] * fi;
         acc[k] += fi * fi;
     }
-    __shared__ double sh[RB / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = 0; k < nd; ++k) {
-        double v = (double)acc[k];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) sh[warp] = v;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int w = 0; w < RB / 32; ++w) s += sh[w];
-            part[(long long)blockIdx.x * nd + k] = s;
-        }
-        __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ND; ++k) out[k] = (double)acc[k];
+}
+
+// per-thread partials of the history Gram for a runtime history length m <= 16
+template <typename T>
+__device__ void gram_accum_dispatch(int m, const T* F, const int* sl, const T* f, T c, long long n, long long lo,
+                                    long long hi, long long step, double* out) {
+    switch (m) {
+#define SDFT_GRAM_CASE(CC) \
+    case CC: gram_accum<CC, T>(F, sl, f, c, n, lo, hi, step, out); break;
+        SDFT_GRAM_CASE(0) SDFT_GRAM_CASE(1) SDFT_GRAM_CASE(2) SDFT_GRAM_CASE(3) SDFT_GRAM_CASE(4) SDFT_GRAM_CASE(5)
+        SDFT_GRAM_CASE(6) SDFT_GRAM_CASE(7) SDFT_GRAM_CASE(8) SDFT_GRAM_CASE(9) SDFT_GRAM_CASE(10) SDFT_GRAM_CASE(11)
+        SDFT_GRAM_CASE(12) SDFT_GRAM_CASE(13) SDFT_GRAM_CASE(14) SDFT_GRAM_CASE(15) SDFT_GRAM_CASE(16)
+#undef SDFT_GRAM_CASE
+        default: break;
     }
 }
 
-// sum partials, solve (F^T F) gamma = F^T f by Gaussian elimination with partial pivoting
-__global__ void anderson_solve_kernel(const double* __restrict__ part, int nblk, int m, double* __restrict__ gamma,
-                                      double* __restrict__ ff) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    constexpr int MM = 16;
-    const int nd = m * (m + 1) / 2 + m + 1;
-    double s[MM * (MM + 1) / 2 + MM + 1];
+// block-reduce nd per-thread values (in `vals`, one per thread slot) into part[blockIdx.x * nd + k]
+template <int NW>
+__device__ void block_reduce_partials(const double* vals, int nd, double* part_row, double (*sh)[NW]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < nd; ++k) {
+        double v = vals[k];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[k][warp] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nd; k += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < NW; ++w) v += sh[k][w];
+        part_row[k] = v;
+    }
+}
+
+constexpr int GRAM_MAXND = 16 * 17 / 2 + 16 + 1;
+
+template <typename T>
+__global__ void __launch_bounds__(RB) anderson_gram_kernel(const T* __restrict__ F, const int* __restrict__ slots,
+                                                           int m, const T* __restrict__ f, T c, long long n,
+                                                           double* __restrict__ part) {
+    __shared__ double sh[GRAM_MAXND][RB / 32];
+    int sl[16];
+    for (int j = 0; j < m; ++j) sl[j] = slots[j];
+    double vals[GRAM_MAXND];
+    const long long step = (long long)gridDim.x * blockDim.x;
+    gram_accum_dispatch<T>(m, F, sl, f, c, n, blockIdx.x * (long long)blockDim.x + threadIdx.x, n, step, vals);
+    const int nd = m * (m + 1) / 2 + m + 1;
+    block_reduce_partials<RB / 32>(vals, nd, part + (long long)blockIdx.x * nd, sh);
+}
+
+// sum partials (one thread per entry, in block order), then solve (F^T F) gamma = F^T f by
+// Gaussian elimination with partial pivoting on one thread
+__device__ void anderson_solve_block(const double* __restrict__ part, int nblk, int m, double* gamma, double* ff) {
+    __shared__ double s[GRAM_MAXND];
+    const int nd = m * (m + 1) / 2 + m + 1;
+    for (int k = threadIdx.x; k < nd; k += blockDim.x) {
         double v = 0.0;
         for (int b = 0; b < nblk; ++b) v += part[(long long)b * nd + k];
         s[k] = v;
     }
-    double G[MM][MM + 1];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double G[16][17];
     int k = 0;
     for (int a = 0; a < m; ++a)
         for (int b = a; b < m; ++b) {
@@ -277,14 +318,14 @@ __global__ void anderson_solve_kernel(const double* __restrict__ part, int nblk,
             ++k;
         }
     for (int a = 0; a < m; ++a) G[a][m] = s[k++];
-    ff[0] = s[k];
+    *ff = s[k];
     for (int col = 0; col < m; ++col) {
         int piv = col;
         for (int r = col + 1; r < m; ++r)
             if (fabs(G[r][col]) > fabs(G[piv][col])) piv = r;
         if (piv != col)
             for (int q = 0; q <= m; ++q) {
-                double t = G[col][q];
+                const double t = G[col][q];
                 G[col][q] = G[piv][q];
                 G[piv][q] = t;
             }
@@ -299,6 +340,11 @@ __global__ void anderson_solve_kernel(const double* __restrict__ part, int nblk,
         for (int q = r + 1; q < m; ++q) v -= G[r][q] * gamma[q];
         gamma[r] = G[r][r] != 0.0 ? v / G[r][r] : 0.0;
     }
+}
+
+__global__ void anderson_solve_kernel(const double* __restrict__ part, int nblk, int m, double* __restrict__ gamma,
+                                      double* __restrict__ ff) {
+    anderson_solve_block(part, nblk, m, gamma, ff);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -645,13 +691,16 @@ template <typename T>
 __global__ void __launch_bounds__(256) laplacian_residual_kernel(const T* __restrict__ x, const T* __restrict__ b,
                                                                  T* __restrict__ out, LapCoef K, int n1, int n2,
                                                                  int n3) {
-    const long long ng = (long long)n1 * n2 * n3;
-    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // 32-bit indices: the grid has < 2^31 points
+    const int plane = n1 * n2;
+    const int ng = plane * n3;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ng) return;
-    const int i = (int)(g % n1);
-    const int j = (int)((g / n1) % n2);
-    const int k = (int)(g / ((long long)n1 * n2));
-    const long long plane = (long long)n1 * n2;
+    const int k = g / plane;
+    const int rem = g - k * plane;
+    const int j = rem / n1;
+    const int i = rem - j * n1;
+    const int row = g - i, col = g - j * n1, pl = g - k * plane;
     T acc = (T)K.c0 * x[g];
 #pragma unroll
     for (int r = 1; r <= FD_RADIUS; ++r) {
@@ -662,9 +711,8 @@ __global__ void __launch_bounds__(256) laplacian_residual_kernel(const T* __rest
         jm += jm < 0 ? n2 : 0;
         kp -= kp >= n3 ? n3 : 0;
         km += km < 0 ? n3 : 0;
-        const long long row = g - i, col = g - (long long)j * n1, pl = g - k * plane;
         acc += (T)K.c[0][r] * (x[row + ip] + x[row + im]);
-        acc += (T)K.c[1][r] * (x[col + (long long)jp * n1] + x[col + (long long)jm * n1]);
+        acc += (T)K.c[1][r] * (x[col + jp * n1] + x[col + jm * n1]);
         acc += (T)K.c[2][r] * (x[pl + kp * plane] + x[pl + km * plane]);
     }
     // -L x = 2 * (-1/2 L x): out = b + L x = b - 2 acc
@@ -760,7 +808,7 @@ int poisson_aar(sdft_ctx* c, const double* f, double* phi, double tol, int max_i
             SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 512, sizeof(int) * count, cudaMemcpyHostToDevice, c->stream));
             const int nblk = 64;
             anderson_gram_kernel<double><<<nblk, RB, 0, c->stream>>>(Fs, slots, count, r, cj, n, part);
-            anderson_solve_kernel<<<1, 32, 0, c->stream>>>(part, nblk, count, gam, ffv);
+            anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part, nblk, count, gam, ffv);
             anderson_update_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(phi, r, cj, beta, Xs, Fs, slots, gam, count, n);
             SDFT_CUDA(cudaGetLastError());
             count_launch(c, 3);
@@ -807,7 +855,7 @@ static int aar_fp32(sdft_ctx* c, const float* b, float* x, double tol_rel, int m
     {
         // ||b||^2 through the history Gram with m = 0 (its last entry is (c f).(c f))
         anderson_gram_kernel<float><<<64, RB, 0, c->stream>>>(Fs, slots, 0, b, 1.0f, n, part);
-        anderson_solve_kernel<<<1, 32, 0, c->stream>>>(part, 64, 0, gam, ffv);
+        anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part, 64, 0, gam, ffv);
         count_launch(c, 2);
         SDFT_CUDA(cudaMemcpyAsync(c->hscal, ffv, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         SDFT_CUDA(cudaStreamSynchronize(c->stream));
@@ -838,7 +886,7 @@ static int aar_fp32(sdft_ctx* c, const float* b, float* x, double tol_rel, int m
             SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 512, sizeof(int) * count, cudaMemcpyHostToDevice, c->stream));
             const int nblk = 64;
             anderson_gram_kernel<float><<<nblk, RB, 0, c->stream>>>(Fs, slots, count, r, cj, n, part);
-            anderson_solve_kernel<<<1, 32, 0, c->stream>>>(part, nblk, count, gam, ffv);
+            anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part, nblk, count, gam, ffv);
             anderson_update_kernel<float><<<nblocks(n), 256, 0, c->stream>>>(x, r, cj, beta, Xs, Fs, slots, gam, count, n);
             SDFT_CUDA(cudaGetLastError());
             count_launch(c, 3);
@@ -858,6 +906,249 @@ static int aar_fp32(sdft_ctx* c, const float* b, float* x, double tol_rel, int m
     }
     *final_rel = rel;
     return it;
+}
+
+// ---------------------------------------------------------------------------------------
+// Persistent FP32 AAR: the whole correction solve A d = b (A = -L_h) in one cooperative launch.
+// CTA k owns points [k*per, (k+1)*per).  Per iteration: residual r = b + L x_cur on own points
+// (neighbours read from L2), history push, then Richardson x_next = x_cur + w c r or, every p-th
+// iteration, Anderson x_next = x_cur + beta c r - sum gamma (X + beta F) with the small Gram
+// reduced through per-block partials (every CTA sums them in the same order and solves the same
+// m x m system).  x is double-buffered, so one grid barrier per iteration separates the reads of
+// x_cur from the writes of x_next (two on Anderson steps).  The barrier spin is bounded: on
+// timeout the kernel records an error status and every CTA returns.
+// ---------------------------------------------------------------------------------------
+struct AarPersistArgs {
+    const float* b;
+    float* x0;       // x buffers (double-buffered)
+    float* x1;
+    float* r;
+    float* xprev;
+    float* fprev;
+    float* Xs;       // [m][n]
+    float* Fs;       // [m][n]
+    double* part;    // [gridDim][ND]
+    unsigned* bar;   // [2]: arrival count, generation
+    int* status;     // [4]: 0 ok / 1 barrier timeout, iterations, final buffer index
+    double* rel_out;
+    LapCoef K;
+    int n1, n2, n3;
+    long long n;
+    float cj, omega, beta;
+    double bnorm2, tol_rel;
+    int max_iter;
+    unsigned expected_blocks;   // arrivals the barrier waits for (== gridDim.x)
+    long long spin_limit;
+};
+
+constexpr int AAR_M = 7, AAR_P = 6, AAR_ND = AAR_M * (AAR_M + 1) / 2 + AAR_M + 1;
+
+__device__ bool grid_barrier(unsigned* bar, unsigned expected, long long limit, int* flag) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == expected - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long i = 0;
+            while (*gen == g) {
+                if (++i > limit || *(volatile int*)flag != 0) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (!ok) atomicExch(flag, 1);
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+constexpr int AAR_BS = 256;    // threads per CTA of the persistent solver (one CTA per SM)
+
+__global__ void __launch_bounds__(AAR_BS) aar_persistent_kernel(AarPersistArgs A) {
+    __shared__ double red[AAR_ND][AAR_BS / 32];
+    __shared__ double gam_s[AAR_M];
+    __shared__ double ff_s;
+    const long long per = (A.n + gridDim.x - 1) / gridDim.x;
+    const long long lo = blockIdx.x * per, hi = min(A.n, lo + per);
+    const long long plane = (long long)A.n1 * A.n2;
+    int head = 0, count = 0;
+    int cur = 0;
+    int it;
+    double rel = 1.0;
+    for (it = 0; it < A.max_iter; ++it) {
+        float* xc = cur ? A.x1 : A.x0;
+        float* xn = cur ? A.x0 : A.x1;
+        const int slot = head;
+        // residual and history push on own points
+        for (long long g = lo + threadIdx.x; g < hi; g += blockDim.x) {
+            const int i = (int)(g % A.n1), j = (int)((g / A.n1) % A.n2), k = (int)(g / plane);
+            float acc = (float)A.K.c0 * xc[g];
+#pragma unroll
+            for (int rr = 1; rr <= FD_RADIUS; ++rr) {
+                int ip = i + rr, im = i - rr, jp = j + rr, jm = j - rr, kp = k + rr, km = k - rr;
+                ip -= ip >= A.n1 ? A.n1 : 0;
+                im += im < 0 ? A.n1 : 0;
+                jp -= jp >= A.n2 ? A.n2 : 0;
+                jm += jm < 0 ? A.n2 : 0;
+                kp -= kp >= A.n3 ? A.n3 : 0;
+                km += km < 0 ? A.n3 : 0;
+                const long long row = g - i, col = g - (long long)j * A.n1, pl = g - k * plane;
+                acc += (float)A.K.c[0][rr] * (xc[row + ip] + xc[row + im]);
+                acc += (float)A.K.c[1][rr] * (xc[col + (long long)jp * A.n1] + xc[col + (long long)jm * A.n1]);
+                acc += (float)A.K.c[2][rr] * (xc[pl + kp * plane] + xc[pl + km * plane]);
+            }
+            const float r = A.b[g] - 2.f * acc;
+            A.r[g] = r;
+            const float fi = A.cj * r;
+            if (it > 0) {
+                A.Xs[(long long)slot * A.n + g] = xc[g] - A.xprev[g];
+                A.Fs[(long long)slot * A.n + g] = fi - A.fprev[g];
+            }
+            A.xprev[g] = xc[g];
+            A.fprev[g] = fi;
+        }
+        if (it > 0) {
+            head = (head + 1) % AAR_M;
+            count = min(count + 1, AAR_M);
+        }
+        const bool anderson = ((it + 1) % AAR_P == 0) && count > 0;
+        if (!anderson) {
+            for (long long g = lo + threadIdx.x; g < hi; g += blockDim.x) xn[g] = xc[g] + A.omega * A.cj * A.r[g];
+        } else {
+            // partial Gram of the history (slots in age order) and F.(c r), (c r).(c r)
+            int sl[AAR_M];
+            for (int jj = 0; jj < count; ++jj) sl[jj] = ((head - count + jj) % AAR_M + AAR_M) % AAR_M;
+            const int nd = count * (count + 1) / 2 + count + 1;
+            double vals[AAR_ND];
+            switch (count) {
+#define SDFT_AAR_CASE(CC) \
+    case CC: gram_accum<CC, float>(A.Fs, sl, A.r, A.cj, A.n, lo + threadIdx.x, hi, blockDim.x, vals); break;
+                SDFT_AAR_CASE(1) SDFT_AAR_CASE(2) SDFT_AAR_CASE(3) SDFT_AAR_CASE(4) SDFT_AAR_CASE(5) SDFT_AAR_CASE(6)
+                SDFT_AAR_CASE(7)
+#undef SDFT_AAR_CASE
+                default: break;
+            }
+            block_reduce_partials<AAR_BS / 32>(vals, nd, A.part + (long long)blockIdx.x * nd, red);
+            if (!grid_barrier(A.bar, A.expected_blocks, A.spin_limit, A.status)) return;
+            anderson_solve_block(A.part, gridDim.x, count, gam_s, &ff_s);
+            __syncthreads();
+            rel = sqrt(ff_s / ((double)A.cj * A.cj) / A.bnorm2);
+            for (long long g = lo + threadIdx.x; g < hi; g += blockDim.x) {
+                float v = xc[g] + A.beta * A.cj * A.r[g];
+                for (int jj = 0; jj < count; ++jj) {
+                    const long long o = (long long)sl[jj] * A.n + g;
+                    v -= (float)gam_s[jj] * (A.Xs[o] + A.beta * A.Fs[o]);
+                }
+                xn[g] = v;
+            }
+        }
+        if (!grid_barrier(A.bar, A.expected_blocks, A.spin_limit, A.status)) return;
+        cur ^= 1;
+        if (anderson && !(rel > A.tol_rel)) {   // converged (also stops on NaN)
+            ++it;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.status[1] = it;
+        A.status[2] = cur;
+        *A.rel_out = rel;
+    }
+}
+
+// FP32 correction solve by the persistent kernel; x (work32 slot) receives the solution.
+static int aar_fp32_persistent(sdft_ctx* c, const float* b, float* x, double tol_rel, int max_iter,
+                               double* final_rel) {
+    const long long n = c->ng;
+    AarPersistArgs A;
+    A.b = b;
+    A.x0 = x;
+    A.x1 = c->work32 + 19 * n;
+    A.r = c->work32 + 1 * n;
+    A.xprev = c->work32 + 2 * n;
+    A.fprev = c->work32 + 3 * n;
+    A.Xs = c->work32 + 4 * n;
+    A.Fs = A.Xs + (long long)AAR_M * n;
+    A.part = c->scal + 4096;
+    A.bar = reinterpret_cast<unsigned*>(c->scal + 40);
+    A.status = reinterpret_cast<int*>(c->scal + 42);
+    A.rel_out = c->scal + 44;
+    for (int r = 0; r <= FD_RADIUS; ++r) {
+        A.K.c[0][r] = c->coef.cx[r];
+        A.K.c[1][r] = c->coef.cy[r];
+        A.K.c[2][r] = c->coef.cz[r];
+    }
+    A.K.c0 = c->coef.c0;
+    A.n1 = c->n[0];
+    A.n2 = c->n[1];
+    A.n3 = c->n[2];
+    A.n = n;
+    A.cj = (float)(1.0 / (2.0 * c->coef.c0));
+    A.omega = 0.6f;
+    A.beta = 0.6f;
+    A.tol_rel = tol_rel;
+    A.max_iter = max_iter;
+    A.spin_limit = 1LL << 24;   // volatile polls of the barrier generation (~0.1-1 s)
+    // ||b||^2
+    {
+        double* part = c->scal + 2048;
+        anderson_gram_kernel<float><<<64, RB, 0, c->stream>>>(A.Fs, nullptr, 0, b, 1.0f, n, part);
+        anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part, 64, 0, c->scal + 64, c->scal + 128);
+        count_launch(c, 2);
+        SDFT_CUDA(cudaMemcpyAsync(c->hscal, c->scal + 128, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+        A.bnorm2 = c->hscal[0];
+    }
+    SDFT_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * n, c->stream));
+    if (A.bnorm2 == 0.0) {
+        *final_rel = 0.0;
+        return 0;
+    }
+    // grid: co-resident CTAs (cooperative launch), at most one per 2048 points, <= 12288 partial slots
+    int dev = 0, nsm = 0, per_sm = 0;
+    SDFT_CUDA(cudaGetDevice(&dev));
+    SDFT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SDFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aar_persistent_kernel, AAR_BS, 0));
+    if (per_sm < 1) {
+        c->aar_persistent = false;
+        return aar_fp32(c, b, x, tol_rel, max_iter, final_rel);
+    }
+    // one CTA per SM (fewer arrivals per barrier, even work), fewer for small grids
+    long long nblk = std::min<long long>((long long)nsm, (n + 1023) / 1024);
+    nblk = std::max<long long>(1, std::min<long long>(nblk, 12288 / AAR_ND));
+    A.expected_blocks = (unsigned)nblk + (c->test_barrier_extra ? 1u : 0u);
+    if (c->test_barrier_extra) A.spin_limit = 200000;
+    SDFT_CUDA(cudaMemsetAsync(A.bar, 0, 2 * sizeof(unsigned), c->stream));
+    SDFT_CUDA(cudaMemsetAsync(A.status, 0, 4 * sizeof(int), c->stream));
+    void* args[] = {&A};
+    const cudaError_t le = cudaLaunchCooperativeKernel((const void*)aar_persistent_kernel, dim3((unsigned)nblk),
+                                                       dim3(AAR_BS), args, 0, c->stream);
+    if (le != cudaSuccess) {
+        // no co-residency guarantee available: fall back to one launch per iteration
+        cudaGetLastError();
+        c->aar_persistent = false;
+        return aar_fp32(c, b, x, tol_rel, max_iter, final_rel);
+    }
+    count_launch(c);
+    int st[4];
+    SDFT_CUDA(cudaMemcpyAsync(st, A.status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaMemcpyAsync(c->hscal, A.rel_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    if (st[0] != 0) throw Error{SDFT_ERR_DEVICE_TIMEOUT, "persistent Poisson solver: grid barrier timed out"};
+    if (st[2] == 1) SDFT_CUDA(cudaMemcpyAsync(x, A.x1, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
+    *final_rel = c->hscal[0];
+    return st[1];
 }
 
 int poisson_mixed(sdft_ctx* c, const double* f, double* phi, double tol, int max_iter) {
@@ -931,7 +1222,8 @@ int poisson_mixed(sdft_ctx* c, const double* f, double* phi, double tol, int max
         count_launch(c);
         double inner_rel = 1.0;
         const double want = std::max(1e-3, 0.3 * tol / rel);
-        total += aar_fp32(c, b32, d32, want, std::min(400, max_iter - total), &inner_rel);
+        total += c->aar_persistent ? aar_fp32_persistent(c, b32, d32, want, std::min(400, max_iter - total), &inner_rel)
+                                   : aar_fp32(c, b32, d32, want, std::min(400, max_iter - total), &inner_rel);
         convert_add_kernel<double, float><<<nblocks(n), 256, 0, c->stream>>>(phi, d32, 1.0, 1.0, n);
         count_launch(c);
     }
@@ -998,7 +1290,7 @@ void pulay_update(sdft_ctx* c) {
         SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 640, sizeof(int) * cnt, cudaMemcpyHostToDevice, c->stream));
         const int nblk = 32;  // 32 x (m(m+1)/2 + m + 1) <= 12288 partials for m <= 16
         anderson_gram_kernel<double><<<nblk, RB, 0, c->stream>>>(c->mix_df, slots, cnt, f, 1.0, n, part);
-        anderson_solve_kernel<<<1, 32, 0, c->stream>>>(part, nblk, cnt, gam, ffv);
+        anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part, nblk, cnt, gam, ffv);
         anderson_update_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(c->rho_in, f, 1.0, c->opt.mix_beta, c->mix_dx,
                                                                   c->mix_df, slots, gam, cnt, n);
         count_launch(c, 3);

@@ -116,6 +116,8 @@ struct sdft_ctx {
     uint64_t launches = 0;
     bool timing = false;
     int stencil_choice[4] = {-1, -1, -1, -1};  // autotuned variant per storage kind
+    bool aar_persistent = true;   // FP32 Poisson corrections in one cooperative launch
+    bool test_barrier_extra = false;  // test hook: the persistent barrier waits for one CTA too many
     std::vector<cudaEvent_t> ev_free;
     std::vector<sdft::PendingTiming> pending;
     sdft_kernel_stats kstat[SDFT_K_COUNT] = {};
