@@ -205,3 +205,40 @@ def uneven_cells(count: int = 32, seed: int = 3) -> list:
         out.append(Cell(f"uneven{c}_{n}", (L, L, L), (n, n, n), np.array(pos), np.zeros(nat, int),
                         [Species()], nstates=nstates_rule(4.0 * nat), cheb_degree=20, seed=seed))
     return out
+
+
+# ---------------------------------------------------------------------------
+# learned initial density: QMD-like configuration sequences and network initialisation
+# ---------------------------------------------------------------------------
+def qmd_lattice64_cell(seed: int, sigma: float = 0.15) -> Cell:
+    """One configuration of the 64-atom sequence: the 4x4x4 lattice (edge 20.52, 80^3 grid,
+    154 states, degree 20) with Gaussian displacements sigma = 0.15 bohr drawn with `seed`."""
+    c = lattice_cell(4, 80, sigma, seed, 20, f"qmd64_{seed}")
+    return c
+
+
+def qmd_lattice8_cell(seed: int, sigma: float = 0.15) -> Cell:
+    """Small member of the same family for tests: 2x2x2 lattice, edge 10.26 bohr, 40^3 grid
+    (h = 0.2565), Gamma point, 20 states, degree 16, displacements sigma = 0.15 bohr."""
+    c = lattice_cell(2, 40, sigma, seed, 16, f"qmd8_{seed}")
+    return c
+
+
+MLP_NFEAT, MLP_HIDDEN = 32, 64
+MLP_NPARAM = MLP_HIDDEN * MLP_NFEAT + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    """Flat FP32 parameter vector (W1 [64x32], b1, W2 [64x64], b2, w3, b3): weights uniform in
+    +-sqrt(6/(fan_in+fan_out)) (Glorot) from uniform_counter(seed, i), biases zero."""
+    sizes = [(MLP_HIDDEN, MLP_NFEAT), (MLP_HIDDEN,), (MLP_HIDDEN, MLP_HIDDEN), (MLP_HIDDEN,), (1, MLP_HIDDEN), (1,)]
+    out, off = [], 0
+    for shp in sizes:
+        n = int(np.prod(shp))
+        if len(shp) == 2:
+            a = math.sqrt(6.0 / (shp[0] + shp[1]))
+            out.append(2.0 * a * uniform_counter(seed, np.arange(off, off + n, dtype=np.uint64)))
+        else:
+            out.append(np.zeros(n))
+        off += n
+    return np.concatenate(out).astype(np.float32)
