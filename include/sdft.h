@@ -278,6 +278,62 @@ sdft_status sdft_set_timing(sdft_ctx* ctx, int on);
 sdft_status sdft_get_kernel_stats(sdft_ctx* ctx, int family, sdft_kernel_stats* out);
 sdft_status sdft_reset_kernel_stats(sdft_ctx* ctx);
 
+/* ---- learned initial density -------------------------------------------------------------
+ * The paper starts the SCF from a superposition of atomic densities (Sec. 2.1) and names machine
+ * learning as a way to improve efficiency (Sec. 4).  Here a small network predicts the correction
+ * rho* - rho_SAD at each grid point; only the SCF's starting point (hence its iteration count)
+ * changes, the converged answer does not.
+ *   Descriptors (Behler-Parrinello radial symmetry functions), j = 0..31:
+ *     G_j(x) = sum_atoms sum_images exp(-(r - mu_j)^2 / (2 eta^2)) (cos(pi r / 6.5) + 1) / 2,
+ *     r = |x - R_a - T| <= 6.5 bohr, mu_j = 6 j / 31, eta = 6 / 31 (bohr).
+ *   Network: h1 = silu(W1 G + b1), h2 = silu(W2 h1 + b2), y = w3 . h2 + b3 (widths 32-64-64-1).
+ *   Parameters: one FP32 vector of SDFT_MLP_NPARAM: W1 [64 x 32] row-major, b1 [64],
+ *     W2 [64 x 64] row-major, b2 [64], w3 [64], b3.  Kernels round the parameters to BF16 and
+ *     compute in FP32 (training keeps the FP32 vector as the master copy).
+ *   Features: device BF16 (uint16 bit patterns) [npts][32], point-major.
+ *   Loss: mean over the batch of (y - t)^2.
+ *   Mini-batches: the batch of size B starting at s visits points perm((s + i) mod npts), i < B,
+ *     with perm(j) = j * P mod npts, P = 1000003 (999983 when 1000003 divides npts).
+ * All pointers below are device pointers unless named *_host; calls are asynchronous on
+ * cuda_stream (a cudaStream_t) or on the context's stream; errors without a context are
+ * reported by sdft_last_error(NULL). */
+#define SDFT_MLP_NFEAT 32
+#define SDFT_MLP_NPARAM 6337
+
+/* Descriptors of every grid point of the context's cell -> feat [ngrid][32]; if target is not
+ * NULL, also target [ngrid] (FP32) = sum over spins of the last SCF's output density minus the
+ * SAD density (the training target once the SCF has converged).  Synchronises the stream. */
+sdft_status sdft_mlp_dataset(sdft_ctx* ctx, uint16_t* feat, float* target);
+
+/* Loss and gradient of one mini-batch: grad [NPARAM] is overwritten with d(loss)/d(params)
+ * (FP32, BF16-rounded parameters in the forward pass); the batch loss is ADDED to *loss (device
+ * double, so that several batches can share one accumulator).  1 <= batch <= npts. */
+sdft_status sdft_mlp_loss_grad(const uint16_t* feat, const float* target, int64_t npts, int64_t batch,
+                               int64_t start, const float* params, float* grad, double* loss,
+                               void* cuda_stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, step >= 1) on params, with
+ * FP32 moments m, v [NPARAM] (zero before step 1). */
+sdft_status sdft_mlp_adam(float* params, const float* grad, float* m, float* v, int step, double lr,
+                          void* cuda_stream);
+
+/* nsteps Adam steps; step first_step + k uses the batch starting at (first_step + k - 1) * batch
+ * (mod npts) and writes its loss (before the update) to loss[k] (device double [nsteps]).
+ * grad [NPARAM] is scratch. */
+sdft_status sdft_mlp_train(const uint16_t* feat, const float* target, int64_t npts, int64_t batch,
+                           float* params, float* grad, float* m, float* v, int first_step, int nsteps,
+                           double lr, double* loss, void* cuda_stream);
+
+/* Inference: y [npts] = network(feat). */
+sdft_status sdft_mlp_forward(const uint16_t* feat, int64_t npts, const float* params, float* y,
+                             void* cuda_stream);
+
+/* Learned guess for the next sdft_scf of this context: rho0 = max(rho_SAD + y, 0) renormalised to
+ * N_e, split over spins as the SAD guess is; it replaces the SAD start like sdft_set_density.
+ * The first call allocates 68 bytes per grid point of scratch (kept until sdft_destroy).
+ * Synchronises the stream. */
+sdft_status sdft_mlp_predict(sdft_ctx* ctx, const float* params);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (SDFT_FP64, SDFT_MIXED, SDFT_GUESS_SAD, SDFT_GUESS_USER, sdft_options,  # noqa: F401
-                   sdft_iter_record, sdft_result)
+                   sdft_iter_record, sdft_result, SDFT_MLP_NFEAT, SDFT_MLP_NPARAM)
 
 __all__ = [
     "SdftError", "Context", "SDFT_FP64", "SDFT_MIXED", "sdft_default_options", "sdft_create", "sdft_destroy",
@@ -23,6 +23,8 @@ __all__ = [
     "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_subspace_matrices_noalloc", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
     "sdft_lanczos_bounds", "sdft_launch_count", "sdft_set_timing", "sdft_get_kernel_stats",
     "sdft_reset_kernel_stats", "pack_block", "unpack_block", "block_shape",
+    "SDFT_MLP_NFEAT", "SDFT_MLP_NPARAM", "sdft_mlp_dataset", "sdft_mlp_loss_grad", "sdft_mlp_adam",
+    "sdft_mlp_train", "sdft_mlp_forward", "sdft_mlp_predict",
 ]
 
 
@@ -317,6 +319,47 @@ def sdft_get_kernel_stats(ctx: Context) -> dict:
 
 def sdft_reset_kernel_stats(ctx: Context):
     _check(_lib.lib().sdft_reset_kernel_stats(ctx.handle), ctx.handle)
+
+
+# ---- learned initial density (see include/sdft.h) -----------------------------------------
+def _stream(stream):
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream if stream is None
+                      else getattr(stream, "cuda_stream", stream))
+
+
+def sdft_mlp_dataset(ctx: Context, feat, target=None):
+    """feat: device int16/uint16 tensor [ngrid, 32] (BF16 bits); target: device float32 [ngrid] or None."""
+    _check(_lib.lib().sdft_mlp_dataset(ctx.handle, _ptr(feat), None if target is None else _ptr(target)),
+           ctx.handle)
+    return feat, target
+
+
+def sdft_mlp_loss_grad(feat, target, npts: int, batch: int, start: int, params, grad, loss, stream=None):
+    _check(_lib.lib().sdft_mlp_loss_grad(_ptr(feat), _ptr(target), npts, batch, start, _ptr(params), _ptr(grad),
+                                         _ptr(loss), _stream(stream)), None)
+    return grad, loss
+
+
+def sdft_mlp_adam(params, grad, m, v, step: int, lr: float, stream=None):
+    _check(_lib.lib().sdft_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), step, lr, _stream(stream)), None)
+    return params
+
+
+def sdft_mlp_train(feat, target, npts: int, batch: int, params, grad, m, v, first_step: int, nsteps: int,
+                   lr: float, loss, stream=None):
+    _check(_lib.lib().sdft_mlp_train(_ptr(feat), _ptr(target), npts, batch, _ptr(params), _ptr(grad), _ptr(m),
+                                     _ptr(v), first_step, nsteps, lr, _ptr(loss), _stream(stream)), None)
+    return loss
+
+
+def sdft_mlp_forward(feat, npts: int, params, y, stream=None):
+    _check(_lib.lib().sdft_mlp_forward(_ptr(feat), npts, _ptr(params), _ptr(y), _stream(stream)), None)
+    return y
+
+
+def sdft_mlp_predict(ctx: Context, params):
+    _check(_lib.lib().sdft_mlp_predict(ctx.handle, _ptr(params)), ctx.handle)
 
 
 # ---- block storage marshalling (see the storage kinds in include/sdft.h) -----------------

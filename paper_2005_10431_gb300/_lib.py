@@ -119,7 +119,17 @@ SIGNATURES = {
     "sdft_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "sdft_get_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(sdft_kernel_stats)]),
     "sdft_reset_kernel_stats": (C.c_int, [C.c_void_p]),
+    "sdft_mlp_dataset": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sdft_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sdft_mlp_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p]),
+    "sdft_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
+    "sdft_mlp_forward": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sdft_mlp_predict": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
+SDFT_MLP_NFEAT = 32
+SDFT_MLP_NPARAM = 6337
 
 
 def library_path() -> str:

@@ -611,6 +611,70 @@ sdft_status sdft_subspace_matrices_noalloc(int precision, int is_complex, const 
     }
 }
 
+#define SDFT_TRY_NOCTX(...)               \
+    try {                                 \
+        sdft::g_create_error.clear();     \
+        __VA_ARGS__;                      \
+        return SDFT_OK;                   \
+    } catch (const Error& e) {            \
+        sdft::g_create_error = e.msg;     \
+        return e.code;                    \
+    }
+
+sdft_status sdft_mlp_dataset(sdft_ctx* c, uint16_t* feat, float* target) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(feat != nullptr, SDFT_ERR_INVALID_ARG, "null feature pointer");
+        sdft::mlp_dataset(c, feat, target);
+    })
+}
+
+sdft_status sdft_mlp_loss_grad(const uint16_t* feat, const float* target, int64_t npts, int64_t batch,
+                               int64_t start, const float* params, float* grad, double* loss, void* st) {
+    SDFT_TRY_NOCTX({
+        SDFT_REQUIRE(feat && target && params && grad && loss, SDFT_ERR_INVALID_ARG, "null pointer");
+        SDFT_REQUIRE(npts >= 1 && batch >= 1 && batch <= npts && start >= 0, SDFT_ERR_INVALID_ARG,
+                     "need 1 <= batch <= npts and start >= 0");
+        sdft::mlp_loss_grad(feat, target, npts, batch, start, params, grad, loss, (cudaStream_t)st);
+    })
+}
+
+sdft_status sdft_mlp_adam(float* params, const float* grad, float* m, float* v, int step, double lr, void* st) {
+    SDFT_TRY_NOCTX({
+        SDFT_REQUIRE(params && grad && m && v, SDFT_ERR_INVALID_ARG, "null pointer");
+        SDFT_REQUIRE(step >= 1 && lr > 0, SDFT_ERR_INVALID_ARG, "need step >= 1 and lr > 0");
+        sdft::mlp_adam(params, grad, m, v, step, lr, (cudaStream_t)st);
+    })
+}
+
+sdft_status sdft_mlp_train(const uint16_t* feat, const float* target, int64_t npts, int64_t batch, float* params,
+                           float* grad, float* m, float* v, int first_step, int nsteps, double lr, double* loss,
+                           void* st) {
+    SDFT_TRY_NOCTX({
+        SDFT_REQUIRE(feat && target && params && grad && m && v && loss, SDFT_ERR_INVALID_ARG, "null pointer");
+        SDFT_REQUIRE(npts >= 1 && batch >= 1 && batch <= npts, SDFT_ERR_INVALID_ARG, "need 1 <= batch <= npts");
+        SDFT_REQUIRE(first_step >= 1 && nsteps >= 0 && lr > 0, SDFT_ERR_INVALID_ARG,
+                     "need first_step >= 1, nsteps >= 0, lr > 0");
+        if (nsteps > 0)
+            sdft::mlp_train(feat, target, npts, batch, params, grad, m, v, first_step, nsteps, lr, loss,
+                            (cudaStream_t)st);
+    })
+}
+
+sdft_status sdft_mlp_forward(const uint16_t* feat, int64_t npts, const float* params, float* y, void* st) {
+    SDFT_TRY_NOCTX({
+        SDFT_REQUIRE(feat && params && y, SDFT_ERR_INVALID_ARG, "null pointer");
+        SDFT_REQUIRE(npts >= 0, SDFT_ERR_INVALID_ARG, "npts < 0");
+        if (npts > 0) sdft::mlp_forward(feat, npts, params, y, (cudaStream_t)st);
+    })
+}
+
+sdft_status sdft_mlp_predict(sdft_ctx* c, const float* params) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(params != nullptr, SDFT_ERR_INVALID_ARG, "null parameter pointer");
+        sdft::mlp_guess(c, params);
+    })
+}
+
 sdft_status sdft_set_timing(sdft_ctx* c, int on) {
     SDFT_TRY(c, {
         sdft::resolve_timing(c);

@@ -167,6 +167,7 @@ struct sdft_ctx {
     double* mix_fprev = nullptr;
     int mix_k = 0, mix_count = 0, mix_head = 0;
     bool user_density = false;
+    void* mlp_scratch = nullptr;  // learned guess: features [ng][32] bf16 + output [ng] (allocated on first use)
 
     // results
     std::vector<sdft_iter_record> log;
@@ -272,5 +273,16 @@ void lanczos(sdft_ctx* c, int spin, int kpt, int steps, double* lower, double* u
 sdft_status run_scf(sdft_ctx* c, sdft_result* out);
 void reset_state(sdft_ctx* c);
 void seed_orbitals(sdft_ctx* c, int precision, bool cplx, void* X, int ncol, uint64_t seed);
+
+// ---- mlp.cu --------------------------------------------------------------------------
+int mlp_nparam();
+void mlp_dataset(sdft_ctx* c, void* feat, float* target);
+void mlp_loss_grad(const void* feat, const float* target, long long npts, long long batch, long long start,
+                   const float* params, float* grad, double* loss, cudaStream_t st);
+void mlp_forward(const void* feat, long long npts, const float* params, float* y, cudaStream_t st);
+void mlp_adam(float* p, const float* g, float* m, float* v, int step, double lr, cudaStream_t st);
+void mlp_train(const void* feat, const float* target, long long npts, long long batch, float* params, float* grad,
+               float* m, float* v, int first_step, int nsteps, double lr, double* loss_dev, cudaStream_t st);
+void mlp_guess(sdft_ctx* c, const float* params);
 
 }  // namespace sdft
