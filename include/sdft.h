@@ -107,6 +107,9 @@ typedef struct {
     int init_guess;            /* SDFT_GUESS_SAD or SDFT_GUESS_USER (see sdft_set_density) */
     double initial_moment;     /* nspin=2: SAD split rho (1 +- m)/2 */
     uint64_t seed;             /* counter-based generator seed for the initial orbitals */
+    int batch_problems;        /* 1: SDFT_MIXED runs the CheFSI passes of all (spin, k) problems of one
+                                  storage kind together (grouped stencil / KB launches, batched
+                                  eigensolve); 0: one problem after another */
 } sdft_options;
 
 /* Per-iteration record of the SCF (paper Sec. 2.1 ".out" progress). */
@@ -228,6 +231,14 @@ sdft_status sdft_subspace_matrices_noalloc(int precision, int is_complex, const 
                                            int64_t ngrid, int ncol, double* m, double* hs,
                                            void* cuda_stream);
 
+/* Generalized Hermitian eigensolve of Rayleigh-Ritz (paper Sec. 2.1): Hs q = lambda M q, FP64,
+ * column-major ncol x ncol device matrices (double2 for is_complex).  M must be positive definite.
+ * On return Hs holds Q (Q^H M Q = I, eigenvector j in column j), eig (device, ncol) ascending; M is
+ * overwritten (scratch).  ncol <= 64 uses the library's one-CTA Cholesky + Jacobi solver (unless
+ * SDFT_EIGEN=0 selects cuSOLVER), larger ncol cuSOLVER sygvd/hegvd, both after diagonal
+ * equilibration.  SDFT_ERR_CHOLESKY if M is not positive definite. */
+sdft_status sdft_subspace_eig(sdft_ctx* ctx, int is_complex, double* m, double* hs, double* eig, int ncol);
+
 /* Rotation x = y Q for an FP64 ncol x ncol column-major Q (double2 for complex), device. */
 sdft_status sdft_rotate(sdft_ctx* ctx, int kpt, int precision, const void* y, const void* q,
                         void* x, int ncol);
@@ -254,6 +265,13 @@ sdft_status sdft_lanczos_bounds(sdft_ctx* ctx, int spin, int kpt, int steps, dou
 
 /* Number of kernel launches the library has issued on this context (for benchmarks). */
 sdft_status sdft_launch_count(const sdft_ctx* ctx, uint64_t* count);
+
+/* Stencil tile variant used by the last fused H Y + Chebyshev step on FP32 blocks of the given
+ * kind (is_complex 0: paired real, 1: complex); *index = -1 and name "" if none ran yet.  The
+ * variant is chosen once per context by timing every compiled tile shape on the first large
+ * filter call (environment SDFT_STENCIL_VARIANT=k forces variant k where it fits the grid).
+ * name (host, cap bytes) receives the variant's name. */
+sdft_status sdft_get_stencil_variant(const sdft_ctx* ctx, int is_complex, int* index, char* name, size_t cap);
 
 /* ---- tracing: per-kernel-family device time (paper Sec. 2.1 ".out ... various timings") -- */
 enum {

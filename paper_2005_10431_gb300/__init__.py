@@ -20,8 +20,8 @@ __all__ = [
     "sdft_scf", "sdft_reset", "sdft_get_eigenvalues", "sdft_get_occupations", "sdft_get_density",
     "sdft_set_density", "sdft_get_forces", "sdft_get_scf_log", "sdft_get_pseudocharge", "sdft_get_sad_density",
     "sdft_set_orbitals", "sdft_get_orbitals", "sdft_set_veff", "sdft_apply_h", "sdft_chebyshev_filter",
-    "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_subspace_matrices_noalloc", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
-    "sdft_lanczos_bounds", "sdft_launch_count", "sdft_set_timing", "sdft_get_kernel_stats",
+    "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_subspace_matrices_noalloc", "sdft_subspace_eig", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
+    "sdft_lanczos_bounds", "sdft_launch_count", "sdft_get_stencil_variant", "sdft_set_timing", "sdft_get_kernel_stats",
     "sdft_reset_kernel_stats", "pack_block", "unpack_block", "block_shape",
     "SDFT_MLP_NFEAT", "SDFT_MLP_NPARAM", "sdft_mlp_dataset", "sdft_mlp_loss_grad", "sdft_mlp_adam",
     "sdft_mlp_train", "sdft_mlp_forward", "sdft_mlp_predict",
@@ -269,6 +269,13 @@ def sdft_subspace_matrices_noalloc(precision: int, is_complex: bool, y, hy, ngri
     return m, hs
 
 
+def sdft_subspace_eig(ctx: Context, is_complex: bool, m, hs, eig, ncol: int):
+    """Hs q = lambda M q on device FP64 matrices; Hs <- Q, eig ascending, M overwritten."""
+    _check(_lib.lib().sdft_subspace_eig(ctx.handle, 1 if is_complex else 0, _ptr(m), _ptr(hs), _ptr(eig), ncol),
+           ctx.handle)
+    return hs, eig
+
+
 def sdft_rotate(ctx: Context, kpt: int, precision: int, y, q, x, ncol: int):
     _check(_lib.lib().sdft_rotate(ctx.handle, kpt, precision, _ptr(y), _ptr(q), _ptr(x), ncol), ctx.handle)
     return x
@@ -301,6 +308,15 @@ def sdft_launch_count(ctx: Context) -> int:
     n = C.c_uint64(0)
     _check(_lib.lib().sdft_launch_count(ctx.handle, C.byref(n)), ctx.handle)
     return n.value
+
+
+def sdft_get_stencil_variant(ctx: Context, is_complex: bool = False):
+    """(index, name) of the FP32 stencil tile variant used by the last filter step (-1, '' if none)."""
+    idx = C.c_int(-1)
+    buf = C.create_string_buffer(64)
+    _check(_lib.lib().sdft_get_stencil_variant(ctx.handle, 1 if is_complex else 0, C.byref(idx), buf, 64),
+           ctx.handle)
+    return idx.value, buf.value.decode()
 
 
 def sdft_set_timing(ctx: Context, on: bool = True):

@@ -51,6 +51,7 @@ class sdft_options(C.Structure):
         ("pulay_period", C.c_int), ("pulay_restart", C.c_int), ("scf_tol", C.c_double), ("max_scf", C.c_int),
         ("precision", C.c_int), ("final_fp64_pass", C.c_int), ("poisson_tol", C.c_double),
         ("init_guess", C.c_int), ("initial_moment", C.c_double), ("seed", C.c_uint64),
+        ("batch_problems", C.c_int),
     ]
 
 
@@ -119,6 +120,8 @@ SIGNATURES = {
     "sdft_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "sdft_get_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(sdft_kernel_stats)]),
     "sdft_reset_kernel_stats": (C.c_int, [C.c_void_p]),
+    "sdft_subspace_eig": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "sdft_get_stencil_variant": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_char_p, C.c_size_t]),
     "sdft_mlp_dataset": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sdft_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),

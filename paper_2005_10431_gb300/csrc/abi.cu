@@ -291,6 +291,7 @@ void sdft_default_options(sdft_options* o) {
     o->init_guess = SDFT_GUESS_SAD;
     o->initial_moment = 0.125;
     o->seed = 0;
+    o->batch_problems = 1;
 }
 
 sdft_status sdft_create(const sdft_cell* cell, const sdft_grid* grid, const sdft_atoms* atoms, int ntypes,
@@ -695,6 +696,31 @@ sdft_status sdft_reset_kernel_stats(sdft_ctx* c) {
         sdft::resolve_timing(c);
         for (int k = 0; k < SDFT_K_COUNT; ++k) c->kstat[k] = sdft_kernel_stats{};
     })
+}
+
+sdft_status sdft_subspace_eig(sdft_ctx* c, int is_complex, double* m, double* hs, double* eig, int ncol) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(m && hs && eig, SDFT_ERR_INVALID_ARG, "null pointer");
+        SDFT_REQUIRE(ncol >= 1 && ncol <= c->opt.nstates, SDFT_ERR_INVALID_ARG,
+                     "ncol must be in [1, nstates] (solver workspace is sized for nstates)");
+        bool any_cplx = false;
+        for (const auto& P : c->probs) any_cplx = any_cplx || P.cplx;
+        SDFT_REQUIRE(!is_complex || any_cplx, SDFT_ERR_INVALID_ARG,
+                     "complex eigensolve needs a context with a complex (k != 0) problem");
+        sdft::generalized_eig(c, is_complex != 0, m, hs, eig, ncol);
+    })
+}
+
+sdft_status sdft_get_stencil_variant(const sdft_ctx* c, int is_complex, int* index, char* name, size_t cap) {
+    if (!c || !index) return SDFT_ERR_INVALID_ARG;
+    const int k = is_complex ? 1 : 0;
+    *index = c->stencil_last[k];
+    if (name && cap > 0) {
+        const char* s = c->stencil_last_name[k] ? c->stencil_last_name[k] : "";
+        std::strncpy(name, s, cap - 1);
+        name[cap - 1] = 0;
+    }
+    return SDFT_OK;
 }
 
 sdft_status sdft_launch_count(const sdft_ctx* c, uint64_t* count) {

@@ -403,6 +403,22 @@ void subspace_gram(sdft_ctx* c, int precision, bool cplx, const void* Y, const v
 
 void generalized_eig(sdft_ctx* c, bool cplx, double* M, double* Hs, double* eig, int ncol) {
     const long long nn = (long long)ncol * ncol;
+    if (c->eig_method < 0 && batched_eig_supported(ncol)) {
+        // small subspace: one-CTA Cholesky + Jacobi solver (no cuSOLVER latency)
+        ensure_ptab(c, 1, 3);
+        c->ptab_host.assign({(void*)M, (void*)Hs, (void*)eig});
+        SDFT_CUDA(cudaMemcpyAsync(c->ptab_dev, c->ptab_host.data(), 3 * sizeof(void*), cudaMemcpyHostToDevice,
+                                  c->stream));
+        double* const* tab = reinterpret_cast<double* const*>(c->ptab_dev);
+        batched_generalized_eig(c, cplx, tab, tab + 1, tab + 2, ncol, 1, c->pinfo_dev);
+        int info = 0;
+        SDFT_CUDA(cudaMemcpyAsync(&info, c->pinfo_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+        if (info != 0)
+            throw Error{SDFT_ERR_CHOLESKY, "subspace overlap matrix not positive definite at column " +
+                                               std::to_string(info - 1)};
+        return;
+    }
     ScopedTimer timer(c, SDFT_K_EIGEN);
     diag_kernel<<<nb(ncol), 256, 0, c->stream>>>(M, c->dscale, ncol, cplx);
     scale_kernel<<<nb(nn), 256, 0, c->stream>>>(M, Hs, c->dscale, ncol, cplx);

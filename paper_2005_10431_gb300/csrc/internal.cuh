@@ -78,6 +78,30 @@ struct PendingTiming {
     double bytes, flops;
 };
 
+// one problem of a grouped row-tile stencil launch (same grid, column count and tile for all)
+struct RowProblem {
+    const float2* Y;
+    const float2* Yprev;
+    float2* Ynext;
+    const float* V;
+    const float2* C;
+    const int* patom;
+    const void* pval;
+    int nslot;
+    float alpha, beta, shift;
+    float phr[3], phi[3];
+};
+// one problem of a grouped KB projection C = gamma beta^H Y
+struct KBProblem {
+    const void* Y;
+    void* C;
+    const int* cnt;
+    const int* idx;
+    const void* val;
+    const double* gamma;
+    int cap;
+};
+
 struct Problem {              // one (spin, k) eigenproblem
     int spin = 0, kpt = 0;
     bool cplx = false;
@@ -112,10 +136,17 @@ struct sdft_ctx {
     std::vector<void*> owned;
     cusolverDnHandle_t solver = nullptr;
     syevjInfo_t syevj_params = nullptr;
-    int eig_method = 0;           // 0: sygvd/hegvd, 1: sygvj (real)
+    int eig_method = -1;          // -1: batched Jacobi for n <= 64 else sygvd/hegvd; 0: sygvd/hegvd; 1: sygvj (real)
+    // device pointer tables of batched launches (grown on demand) and their host staging copy
+    void** ptab_dev = nullptr;
+    int* pinfo_dev = nullptr;
+    int ptab_cap = 0;
+    std::vector<void*> ptab_host;
     uint64_t launches = 0;
     bool timing = false;
     int stencil_choice[4] = {-1, -1, -1, -1};  // autotuned variant per storage kind
+    int stencil_last[4] = {-1, -1, -1, -1};    // variant of the last launch per storage kind
+    const char* stencil_last_name[4] = {nullptr, nullptr, nullptr, nullptr};
     bool aar_persistent = true;   // FP32 Poisson corrections in one cooperative launch
     bool test_barrier_extra = false;  // test hook: the persistent barrier waits for one CTA too many
     std::vector<cudaEvent_t> ev_free;
@@ -168,6 +199,17 @@ struct sdft_ctx {
     int mix_k = 0, mix_count = 0, mix_head = 0;
     bool user_density = false;
     void* mlp_scratch = nullptr;  // learned guess: features [ng][32] bf16 + output [ng] (allocated on first use)
+
+    // batched CheFSI (allocated on first use): per problem 3 filter blocks, M, Hs, KB coefficients;
+    // device step tables of the grouped launches and their host copies
+    std::vector<void*> g_blk;
+    std::vector<double*> g_M, g_H;
+    std::vector<void*> g_C;
+    sdft::RowProblem* g_rtab = nullptr;
+    sdft::KBProblem* g_ktab = nullptr;
+    int g_tab_cap = 0;
+    std::vector<sdft::RowProblem> g_rtab_h;
+    std::vector<sdft::KBProblem> g_ktab_h;
 
     // results
     std::vector<sdft_iter_record> log;
@@ -273,6 +315,21 @@ void lanczos(sdft_ctx* c, int spin, int kpt, int steps, double* lower, double* u
 sdft_status run_scf(sdft_ctx* c, sdft_result* out);
 void reset_state(sdft_ctx* c);
 void seed_orbitals(sdft_ctx* c, int precision, bool cplx, void* X, int ncol, uint64_t seed);
+
+// grouped FP32 stencil / KB projection over problems sharing the grid (stencil_f32.cu);
+// grp: device tables.  group_variant_f32 returns -1 when no row tile fits the grid.
+int group_variant_f32(sdft_ctx* c, bool cplx, int ncolE);
+void launch_group_step_f32(sdft_ctx* c, bool cplx, int variant, const RowProblem* grp, int nprob, int ncolE,
+                           bool prev, bool haskb);
+void launch_group_project_f32(sdft_ctx* c, bool cplx, const KBProblem* grp, int nprob, int ncolE);
+
+// ---- batched.cu ----------------------------------------------------------------------
+bool batched_eig_supported(int n);
+// Ms/Hss/eigs: device arrays of `count` device pointers; info: device int[count]
+void batched_generalized_eig(sdft_ctx* c, bool cplx, double* const* Ms, double* const* Hss, double* const* eigs,
+                             int n, int count, int* info);
+// device pointer table with room for `count` entries of `width` pointers (+ count ints of info)
+void ensure_ptab(sdft_ctx* c, int count, int width);
 
 // ---- mlp.cu --------------------------------------------------------------------------
 int mlp_nparam();

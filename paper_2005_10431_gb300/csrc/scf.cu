@@ -315,6 +315,152 @@ static void chefsi_pass(sdft_ctx* c, Problem& P, int precision, void* X) {
     P.cutoff = e2[1];
 }
 
+// ---- batched CheFSI: all problems of one storage kind in grouped launches -------------------
+// Per Chebyshev step one grouped KB projection and one grouped row-tile stencil launch cover every
+// problem; the H Y of Rayleigh-Ritz likewise; then Gram matrices per problem, one batched
+// eigensolve for all problems, rotations per problem, and one host read of all Ritz bounds.
+static void ensure_group_buffers(sdft_ctx* c, int nprob, bool cplx) {
+    const int ns = c->opt.nstates;
+    if ((int)c->g_M.size() >= nprob) return;
+    const size_t bytes = block_elems_bytes(c, SDFT_MIXED, cplx, ns);
+    const int w2 = cplx ? 2 : 1;
+    for (int p = (int)c->g_M.size(); p < nprob; ++p) {
+        for (int i = 0; i < 3; ++i) c->g_blk.push_back(ctx_alloc(c, bytes));
+        c->g_M.push_back((double*)ctx_alloc(c, sizeof(double) * ns * ns * w2));
+        c->g_H.push_back((double*)ctx_alloc(c, sizeof(double) * ns * ns * w2));
+        c->g_C.push_back(ctx_alloc(c, sizeof(float2) * (size_t)std::max(1, c->natom) * ns));
+    }
+}
+
+static void chefsi_pass_group(sdft_ctx* c, const std::vector<Problem*>& G, int variant) {
+    const int ns = c->opt.nstates, m = c->opt.cheb_degree;
+    const int np = (int)G.size();
+    const bool cplx = G[0]->cplx;
+    const int ncolE = cplx ? ns : ns / 2;
+    const long long ng = c->ng;
+    ensure_group_buffers(c, np, cplx);
+    const int ntab = (m + 1) * np;
+    if (c->g_tab_cap < ntab) {
+        c->g_rtab = (RowProblem*)ctx_alloc(c, sizeof(RowProblem) * ntab);
+        c->g_ktab = (KBProblem*)ctx_alloc(c, sizeof(KBProblem) * ntab);
+        c->g_tab_cap = ntab;
+    }
+    c->g_rtab_h.assign(ntab, RowProblem{});
+    c->g_ktab_h.assign(ntab, KBProblem{});
+    bool haskb = false;
+    for (int p = 0; p < np; ++p) {
+        const Problem& P = *G[p];
+        const double a = P.cutoff, b = P.upper, a0 = P.lower;
+        SDFT_REQUIRE(b > a && a > a0, SDFT_ERR_INVALID_ARG, "filter bounds must satisfy a0 < a < b");
+        const KBTables& kb = c->kb[P.kpt];
+        haskb = haskb || kb.S > 0;
+        float2* ring[3] = {(float2*)c->g_blk[3 * p], (float2*)c->g_blk[3 * p + 1], (float2*)c->g_blk[3 * p + 2]};
+        auto slot = [&](int k) -> float2* { return ring[(((2 - (m - k)) % 3) + 3) % 3]; };
+        const float2* X = (const float2*)P.X;
+        float2* Cp = (float2*)c->g_C[p];
+        RowProblem base{};
+        base.V = c->veff32 + (long long)P.spin * ng;
+        base.C = Cp;
+        base.patom = kb.patom;
+        base.pval = kb.pval32;
+        base.nslot = kb.S;
+        for (int d = 0; d < 3; ++d) {
+            const double kd = c->kpts.empty() ? 0.0 : c->kpts[3 * P.kpt + d];
+            base.phr[d] = (float)cos(2.0 * M_PI * kd);
+            base.phi[d] = (float)sin(2.0 * M_PI * kd);
+        }
+        KBProblem kbase{nullptr, Cp, kb.cnt, kb.idx, kb.val32, kb.gamma, kb.cap};
+        const double e = 0.5 * (b - a), cc = 0.5 * (b + a);
+        const double sigma1 = e / (a0 - cc);
+        double sigma = sigma1;
+        for (int k = 1; k <= m; ++k) {
+            RowProblem r = base;
+            r.Y = k == 1 ? X : slot(k - 1);
+            r.Yprev = k == 1 ? nullptr : (k == 2 ? X : slot(k - 2));
+            r.Ynext = slot(k);
+            double alpha, beta = 0.0;
+            if (k == 1) {
+                alpha = sigma1 / e;
+            } else {
+                const double sigma2 = 1.0 / (2.0 / sigma1 - sigma);
+                alpha = 2.0 * sigma2 / e;
+                beta = sigma * sigma2;
+                sigma = sigma2;
+            }
+            r.alpha = (float)alpha;
+            r.beta = (float)beta;
+            r.shift = (float)cc;
+            c->g_rtab_h[(k - 1) * np + p] = r;
+            KBProblem kp = kbase;
+            kp.Y = r.Y;
+            c->g_ktab_h[(k - 1) * np + p] = kp;
+        }
+        // H Y of Rayleigh-Ritz: Y = slot(m) -> HY in the first free ring buffer
+        RowProblem r = base;
+        r.Y = slot(m);
+        r.Yprev = nullptr;
+        r.Ynext = slot(m - 1) == slot(m) ? slot(m - 2) : slot(m - 1);
+        r.alpha = 1.f;
+        r.beta = 0.f;
+        r.shift = 0.f;
+        c->g_rtab_h[m * np + p] = r;
+        KBProblem kp = kbase;
+        kp.Y = r.Y;
+        c->g_ktab_h[m * np + p] = kp;
+    }
+    SDFT_CUDA(cudaMemcpyAsync(c->g_rtab, c->g_rtab_h.data(), sizeof(RowProblem) * ntab, cudaMemcpyHostToDevice,
+                              c->stream));
+    SDFT_CUDA(cudaMemcpyAsync(c->g_ktab, c->g_ktab_h.data(), sizeof(KBProblem) * ntab, cudaMemcpyHostToDevice,
+                              c->stream));
+    // filter (m steps) and H Y, every problem per launch
+    for (int k = 0; k <= m; ++k) {
+        if (haskb) launch_group_project_f32(c, cplx, c->g_ktab + (size_t)k * np, np, ncolE);
+        launch_group_step_f32(c, cplx, variant, c->g_rtab + (size_t)k * np, np, ncolE, k > 0 && k < m, haskb);
+    }
+    // Gram matrices per problem, one batched eigensolve, rotations per problem
+    for (int p = 0; p < np; ++p) {
+        const RowProblem& r = c->g_rtab_h[m * np + p];
+        subspace_gram(c, SDFT_MIXED, cplx, r.Y, r.Ynext, c->g_M[p], c->g_H[p], ns);
+    }
+    if (batched_eig_supported(ns)) {
+        ensure_ptab(c, np, 3);
+        c->ptab_host.resize(3 * np);
+        for (int p = 0; p < np; ++p) {
+            c->ptab_host[p] = c->g_M[p];
+            c->ptab_host[np + p] = c->g_H[p];
+            c->ptab_host[2 * np + p] = G[p]->eig;
+        }
+        SDFT_CUDA(cudaMemcpyAsync(c->ptab_dev, c->ptab_host.data(), sizeof(void*) * 3 * np, cudaMemcpyHostToDevice,
+                                  c->stream));
+        double* const* tab = reinterpret_cast<double* const*>(c->ptab_dev);
+        batched_generalized_eig(c, cplx, tab, tab + np, tab + 2 * np, ns, np, c->pinfo_dev);
+        std::vector<int> info(np);
+        SDFT_CUDA(cudaMemcpyAsync(info.data(), c->pinfo_dev, sizeof(int) * np, cudaMemcpyDeviceToHost, c->stream));
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+        for (int p = 0; p < np; ++p)
+            if (info[p] != 0) throw Error{SDFT_ERR_CHOLESKY, "subspace overlap matrix not positive definite"};
+    } else {
+        for (int p = 0; p < np; ++p) generalized_eig(c, cplx, c->g_M[p], c->g_H[p], G[p]->eig, ns);
+    }
+    for (int p = 0; p < np; ++p) {
+        const RowProblem& r = c->g_rtab_h[m * np + p];
+        rotate_block(c, SDFT_MIXED, cplx, r.Y, c->g_H[p], G[p]->X, ns);
+    }
+    std::vector<double> e2(2 * np);
+    for (int p = 0; p < np; ++p) {
+        SDFT_CUDA(cudaMemcpyAsync(&e2[2 * p], G[p]->eig, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        SDFT_CUDA(cudaMemcpyAsync(&e2[2 * p + 1], G[p]->eig + ns - 1, sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->stream));
+    }
+    SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    for (int p = 0; p < np; ++p) {
+        if (!std::isfinite(e2[2 * p]) || !std::isfinite(e2[2 * p + 1]))
+            throw Error{SDFT_ERR_NONFINITE, "Ritz values are not finite"};
+        G[p]->lower = e2[2 * p];
+        G[p]->cutoff = e2[2 * p + 1];
+    }
+}
+
 struct Energies {
     double F, mu, ts, eband;
 };
@@ -387,6 +533,22 @@ sdft_status run_scf(sdft_ctx* c, sdft_result* out) {
     sdft_status status = SDFT_OK;
     Energies E{};
     const int prec = c->opt.precision;
+    // batched CheFSI: problems of one storage kind that a grouped row-tile launch fits
+    std::vector<Problem*> groups[2], single;
+    int group_var[2] = {-1, -1};
+    bool batched = false;
+    if (prec == SDFT_MIXED && c->opt.batch_problems && c->probs.size() > 1) {
+        for (int k = 0; k < 2; ++k) {
+            const int ncolE = k ? c->opt.nstates : c->opt.nstates / 2;
+            group_var[k] = group_variant_f32(c, k == 1, ncolE);
+        }
+        for (Problem& P : c->probs) {
+            const int k = P.cplx ? 1 : 0;
+            if (group_var[k] >= 0) groups[k].push_back(&P);
+            else single.push_back(&P);
+        }
+        batched = !groups[0].empty() || !groups[1].empty();
+    }
     for (it = 0; it < c->opt.max_scf; ++it) {
         // potentials from rho_in (paper Sec. 2.1: Poisson by AAR, then V_eff = phi + V_xc)
         double ta = now_s();
@@ -412,10 +574,21 @@ sdft_status run_scf(sdft_ctx* c, sdft_result* out) {
                 P.cutoff = lo + 0.1 * (up - lo);
                 P.have_bounds = true;
             }
+            if (batched) continue;   // passes run below, all problems together
             const int passes = it == 0 ? std::max(1, c->opt.first_scf_filter_passes) : 1;
             for (int p = 0; p < passes; ++p) {
                 ta = now_s();
                 chefsi_pass(c, P, prec, P.X);
+                t_filter += now_s() - ta;
+            }
+        }
+        if (batched) {
+            const int passes = it == 0 ? std::max(1, c->opt.first_scf_filter_passes) : 1;
+            for (int p = 0; p < passes; ++p) {
+                ta = now_s();
+                for (int k = 0; k < 2; ++k)
+                    if (!groups[k].empty()) chefsi_pass_group(c, groups[k], group_var[k]);
+                for (Problem* P : single) chefsi_pass(c, *P, prec, P->X);
                 t_filter += now_s() - ta;
             }
         }

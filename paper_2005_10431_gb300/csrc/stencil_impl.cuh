@@ -377,13 +377,304 @@ cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __rest
     cp_async_wait<0>();
 }
 
+// ---- row-tile variant (FP32 blocks, n1 even) --------------------------------------------
+// A CTA owns TY whole x-rows (n1 points, two consecutive points per thread, one 16-byte vector)
+// and marches along z for one element-column.  Because the tile spans the full x extent, the x
+// halo is the row's own periodic wrap: the threads at both row ends copy their points into
+// 6-point pads on the far side of the shared-memory row (with the Bloch phase for complex
+// blocks), so no x-halo is read from memory.  The 12 y-halo rows (with their pads) are
+// staged by cp.async 16-byte copies in a D-stage ring; z-neighbours come from a register queue
+// of 16-byte vectors.  Per-point operands (V, KB slots, Yprev) are read straight from L2.
+constexpr int ROW_HALO_UNITS_PER_THREAD = 4;
+
+
+template <bool CPLX, int TY, int PF, int MAXT, int MINB, int D, bool PREV, bool KB, bool VLOC>
+__global__ void __launch_bounds__(MAXT, MINB)
+cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_, float2* __restrict__ Ynext_,
+                const float* __restrict__ V_, const float2* __restrict__ C_, const int* __restrict__ patom_,
+                const void* __restrict__ pval_, const int nslot_, const StepArgs<float> A, const int ncolE,
+                const RowProblem* __restrict__ grp) {
+    // one problem, or (grp != null) problem blockIdx.z / (ncolE nzc) of a grouped launch
+    const float2* __restrict__ Y = Y_;
+    const float2* __restrict__ Yprev = Yprev_;
+    float2* __restrict__ Ynext = Ynext_;
+    const float* __restrict__ V = V_;
+    const float2* __restrict__ C = C_;
+    const int* __restrict__ patom = patom_;
+    const void* __restrict__ pval = pval_;
+    int nslot = nslot_;
+    float alpha = A.alpha, beta = A.beta, shift = A.shift;
+    float phr[3] = {A.phr[0], A.phr[1], A.phr[2]}, phi[3] = {A.phi[0], A.phi[1], A.phi[2]};
+    int zlin = blockIdx.z;
+    if (grp) {
+        const int prob = blockIdx.z / (ncolE * A.nzc);
+        zlin -= prob * ncolE * A.nzc;
+        const RowProblem& P = grp[prob];
+        Y = P.Y;
+        Yprev = P.Yprev;
+        Ynext = P.Ynext;
+        V = P.V;
+        C = P.C;
+        patom = P.patom;
+        pval = P.pval;
+        nslot = P.nslot;
+        alpha = P.alpha;
+        beta = P.beta;
+        shift = P.shift;
+        for (int d = 0; d < 3; ++d) {
+            phr[d] = P.phr[d];
+            phi[d] = P.phi[d];
+        }
+    }
+    using KV = typename std::conditional<CPLX, float2, float>::type;
+    constexpr int R = FD_RADIUS;
+    constexpr int QN = 2 * R + 1 + PF;
+    constexpr int K = ROW_HALO_UNITS_PER_THREAD;
+    const int HX = blockDim.x;                 // n1 / 2
+    const int n1 = A.n1;
+    const int RS = n1 + 2 * R;                 // shared row stride (float2), even
+    const int SE = (TY + 2 * R) * RS;          // one stage (float2)
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int NT = HX * TY, tid = ty * HX + tx;
+    constexpr int SP = 3;                      // KB slots staged per point (more are read directly)
+    using KV2 = typename std::conditional<CPLX, float4, float2>::type;   // KB values of two points
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    float2* tiles = reinterpret_cast<float2*>(dyn_smem);
+    // per-stage operands of the thread's two points: Yprev, V, KB slots (atom, value)
+    unsigned char* opbase = dyn_smem + sizeof(float2) * (size_t)D * SE;
+    const int opstride = (NT * (16 + 8 + SP * 8 + SP * (int)sizeof(KV2)) + 15) & ~15;   // 16-byte aligned stages
+    float2* Cs = reinterpret_cast<float2*>(opbase + (size_t)D * opstride);
+    auto op_prev = [&](int st) { return reinterpret_cast<float4*>(opbase + st * opstride) + tid; };
+    auto op_v = [&](int st) { return reinterpret_cast<float2*>(opbase + st * opstride + NT * 16) + tid; };
+    auto op_kat = [&](int st, int k) {
+        return reinterpret_cast<int2*>(opbase + st * opstride + NT * 24) + k * NT + tid;
+    };
+    auto op_kval = [&](int st, int k) {
+        return reinterpret_cast<KV2*>(opbase + st * opstride + NT * (24 + SP * 8)) + k * NT + tid;
+    };
+    const int y0 = blockIdx.x * TY;
+    const int col = zlin / A.nzc;
+    const int zc = zlin - col * A.nzc;
+    const int z0 = zc * A.zchunk;
+    const int z1 = min(A.n3, z0 + A.zchunk);
+    const long long plane = (long long)n1 * A.n2;
+    const float2* __restrict__ Yc = Y + (long long)col * A.ng;
+    const int gy = y0 + ty, gx = 2 * tx;
+    const long long gxy = (long long)gy * n1 + gx;
+    if (KB)
+        for (int i = tid; i < A.natom; i += NT) Cs[i] = C[(long long)col * A.natom + i];
+
+    // y-halo units (two points each): 12 rows x (HX interior + 3 left-pad + 3 right-pad)
+    int hdst[K], hsrc[K];
+    float2 hph[K];
+    const int upr = HX + 6;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int u = tid + k * NT;
+        hdst[k] = -1;
+        hsrc[k] = 0;
+        hph[k] = make_float2(1.f, 0.f);
+        if (u < 2 * R * upr) {
+            const int hr = u / upr, j = u - hr * upr;
+            const int trow = hr < R ? hr : TY + hr;          // tile row
+            int tyw;
+            const int wy = wrapi(y0 - R + trow, A.n2, tyw);
+            int x, entry, txw = 0;
+            if (j < HX) { x = 2 * j; entry = R + 2 * j; }
+            else if (j < HX + 3) { x = n1 - R + 2 * (j - HX); entry = 2 * (j - HX); txw = -1; }
+            else { x = 2 * (j - HX - 3); entry = n1 + R + 2 * (j - HX - 3); txw = 1; }
+            hdst[k] = trow * RS + entry;
+            hsrc[k] = wy * n1 + x;
+            if constexpr (CPLX) {
+                float2 ph = make_float2(1.f, 0.f);
+                if (txw) ph = apply_phase<float2, float>(ph, txw, phr[0], phi[0]);
+                if (tyw) ph = apply_phase<float2, float>(ph, tyw, phr[1], phi[1]);
+                hph[k] = ph;
+            }
+        }
+    }
+    float2 phxp = make_float2(1.f, 0.f), phxm = make_float2(1.f, 0.f);   // x wrap +1 / -1
+    if constexpr (CPLX) {
+        phxp = make_float2(phr[0], phi[0]);
+        phxm = make_float2(phr[0], -phi[0]);
+    }
+
+    const float2* __restrict__ Pc = Yprev + (long long)col * A.ng;
+    auto issue = [&](int z, int st) {
+        if (z < z1) {
+            float2* T = tiles + st * SE;
+            const long long off = (long long)z * plane;
+            const float2* src = Yc + off;
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (hdst[k] >= 0) cp_async<16>(T + hdst[k], src + hsrc[k]);
+            const long long g = off + gxy;
+            if (PREV) cp_async<16>(op_prev(st), Pc + g);
+            if (VLOC) cp_async<8>(op_v(st), V + g);
+            if (KB) {
+#pragma unroll
+                for (int k = 0; k < SP; ++k)
+                    if (k < nslot) {
+                        cp_async<8>(op_kat(st, k), patom + k * A.ng + g);
+                        cp_async<sizeof(KV2)>(op_kval(st, k), reinterpret_cast<const KV*>(pval) + k * A.ng + g);
+                    }
+            }
+        }
+        cp_async_commit();
+    };
+    auto ld4 = [](const float2* p) { return *reinterpret_cast<const float4*>(p); };
+    auto cm = [](float4 v, float2 ph) {
+        const float2 a = cmul(make_float2(v.x, v.y), ph), b = cmul(make_float2(v.z, v.w), ph);
+        return make_float4(a.x, a.y, b.x, b.y);
+    };
+
+    float4 q[QN];
+    ZTrack zq;
+    {
+        ZTrack t;
+        ztrack_init(t, z0 - R, A.n3, plane);
+#pragma unroll
+        for (int s2 = 0; s2 < 2 * R + PF; ++s2) {
+            float4 v = ld4(Yc + t.off + gxy);
+            if constexpr (CPLX)
+                if (t.tz) v = cm(v, apply_phase<float2, float>(make_float2(1.f, 0.f), t.tz, phr[2], phi[2]));
+            q[s2] = v;
+            ztrack_next(t, A.n3, plane);
+        }
+        zq = t;
+    }
+#pragma unroll
+    for (int d = 0; d < D - 1; ++d) issue(z0 + d, d);
+
+    const int own = (R + ty) * RS + R + gx;   // this thread's first point in a stage
+    for (int zb = z0; zb < z1; zb += QN) {
+#pragma unroll
+        for (int ph = 0; ph < QN; ++ph) {
+            const int z = zb + ph;
+            if (z < z1) {
+                float2* T = tiles + ((z - z0) % D) * SE;
+                const float4 cen = q[(ph + R) % QN];
+                cp_async_wait<D - 2>();
+                *reinterpret_cast<float4*>(T + own) = cen;
+                if (tx < 3) *reinterpret_cast<float4*>(T + own + n1) = CPLX ? cm(cen, phxp) : cen;
+                if (tx >= HX - 3) *reinterpret_cast<float4*>(T + own - n1) = CPLX ? cm(cen, phxm) : cen;
+                if constexpr (CPLX) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k)
+                        if (hdst[k] >= 0 && (hph[k].x != 1.f || hph[k].y != 0.f)) {
+                            float4* p = reinterpret_cast<float4*>(T + hdst[k]);
+                            *p = cm(*p, hph[k]);
+                        }
+                }
+                {
+                    float4 v = ld4(Yc + zq.off + gxy);
+                    if constexpr (CPLX)
+                        if (zq.tz)
+                            v = cm(v, apply_phase<float2, float>(make_float2(1.f, 0.f), zq.tz, phr[2], phi[2]));
+                    q[(ph + 2 * R + PF) % QN] = v;
+                    ztrack_next(zq, A.n3, plane);
+                }
+                __syncthreads();
+                issue(z + D - 1, (z - z0 + D - 1) % D);
+
+                const float2 c0 = make_float2(cen.x, cen.y), c1 = make_float2(cen.z, cen.w);
+                float2 a0 = efma(A.c0, c0, ezero<float2>());
+                float2 a1 = efma(A.c0, c1, ezero<float2>());
+                {   // x: six 16-byte reads cover x-6 .. x+7
+                    const float4 L0 = ld4(T + own - 6), L1 = ld4(T + own - 4), L2 = ld4(T + own - 2);
+                    const float4 R0 = ld4(T + own + 2), R1 = ld4(T + own + 4), R2 = ld4(T + own + 6);
+#define LO(v) make_float2(v.x, v.y)
+#define HI(v) make_float2(v.z, v.w)
+                    a0 = efma(A.cx[1], eadd(HI(L2), c1), a0);
+                    a0 = efma(A.cx[2], eadd(LO(L2), LO(R0)), a0);
+                    a0 = efma(A.cx[3], eadd(HI(L1), HI(R0)), a0);
+                    a0 = efma(A.cx[4], eadd(LO(L1), LO(R1)), a0);
+                    a0 = efma(A.cx[5], eadd(HI(L0), HI(R1)), a0);
+                    a0 = efma(A.cx[6], eadd(LO(L0), LO(R2)), a0);
+                    a1 = efma(A.cx[1], eadd(c0, LO(R0)), a1);
+                    a1 = efma(A.cx[2], eadd(HI(L2), HI(R0)), a1);
+                    a1 = efma(A.cx[3], eadd(LO(L2), LO(R1)), a1);
+                    a1 = efma(A.cx[4], eadd(HI(L1), HI(R1)), a1);
+                    a1 = efma(A.cx[5], eadd(LO(L1), LO(R2)), a1);
+                    a1 = efma(A.cx[6], eadd(HI(L0), HI(R2)), a1);
+                }
+#pragma unroll
+                for (int r = 1; r <= R; ++r) {
+                    const float4 up = ld4(T + own - r * RS), dn = ld4(T + own + r * RS);
+                    const float4 zu = q[(ph + R + r) % QN], zd = q[(ph + R - r + QN) % QN];
+                    a0 = efma(A.cy[r], eadd(LO(up), LO(dn)), a0);
+                    a1 = efma(A.cy[r], eadd(HI(up), HI(dn)), a1);
+                    a0 = efma(A.cz[r], eadd(LO(zu), LO(zd)), a0);
+                    a1 = efma(A.cz[r], eadd(HI(zu), HI(zd)), a1);
+                }
+                const long long g = (long long)z * plane + gxy;
+                const int st = (z - z0) % D;
+                if (VLOC) {
+                    const float2 v = *op_v(st);
+                    a0 = efma(v.x, c0, a0);
+                    a1 = efma(v.y, c1, a1);
+                }
+                if (KB) {
+                    auto kb_add = [&](int2 at, KV2 kv) {
+                        if constexpr (CPLX) {
+                            if (at.x >= 0) a0 = eadd(a0, cmul(LO(kv), Cs[at.x]));
+                            if (at.y >= 0) a1 = eadd(a1, cmul(HI(kv), Cs[at.y]));
+                        } else {
+                            if (at.x >= 0) a0 = efma(kv.x, Cs[at.x], a0);
+                            if (at.y >= 0) a1 = efma(kv.y, Cs[at.y], a1);
+                        }
+                    };
+#pragma unroll
+                    for (int k = 0; k < SP; ++k)
+                        if (k < nslot) kb_add(*op_kat(st, k), *op_kval(st, k));
+                    for (int k = SP; k < nslot; ++k) {   // slots beyond the staged ones: straight from L2
+                        const int2 at = __ldg(reinterpret_cast<const int2*>(patom + k * A.ng + g));
+                        if (at.x < 0 && at.y < 0) break;   // unused slots (-1) sit at the end
+                        kb_add(at, __ldg(reinterpret_cast<const KV2*>(reinterpret_cast<const KV*>(pval) + k * A.ng + g)));
+                    }
+                }
+                float2 o0 = efma(alpha, efma(-shift, c0, a0), ezero<float2>());
+                float2 o1 = efma(alpha, efma(-shift, c1, a1), ezero<float2>());
+                if (PREV) {
+                    const float4 pv = *op_prev(st);
+                    o0 = efma(-beta, LO(pv), o0);
+                    o1 = efma(-beta, HI(pv), o1);
+                }
+                *reinterpret_cast<float4*>(Ynext + (long long)col * A.ng + g) = make_float4(o0.x, o0.y, o1.x, o1.y);
+#undef LO
+#undef HI
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
 // KB projection: C[col][a] = gamma_a * sum_j conj(beta_a(j)) Y[idx_j, col], NC columns per CTA
 template <typename E, bool CPLX, int NC>
 __global__ void __launch_bounds__(256)
-kb_project_kernel(const E* __restrict__ Y, E* __restrict__ C, const int* __restrict__ cnt,
-                  const int* __restrict__ idx, const void* __restrict__ val,
-                  const double* __restrict__ gamma, int cap, int natom, int ncolE, long long ng) {
+kb_project_kernel(const E* __restrict__ Y_, E* __restrict__ C_, const int* __restrict__ cnt_,
+                  const int* __restrict__ idx_, const void* __restrict__ val_,
+                  const double* __restrict__ gamma_, int cap_, int natom, int ncolE, long long ng,
+                  const KBProblem* __restrict__ grp) {
     using S = typename Elem<E>::S;
+    // one problem, or (grp != null) problem blockIdx.z of a grouped launch
+    const E* __restrict__ Y = Y_;
+    E* __restrict__ C = C_;
+    const int* __restrict__ cnt = cnt_;
+    const int* __restrict__ idx = idx_;
+    const void* __restrict__ val = val_;
+    const double* __restrict__ gamma = gamma_;
+    int cap = cap_;
+    if (grp) {
+        const KBProblem& P = grp[blockIdx.z];
+        Y = reinterpret_cast<const E*>(P.Y);
+        C = reinterpret_cast<E*>(P.C);
+        cnt = P.cnt;
+        idx = P.idx;
+        val = P.val;
+        gamma = P.gamma;
+        cap = P.cap;
+    }
     const int a = blockIdx.x;
     const int c0 = blockIdx.y * NC;
     const int m = cnt[a];
@@ -514,31 +805,117 @@ void launch_variant(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, 
     count_launch(c);
 }
 
+// dynamic shared memory of the row tile: D stages of the halo'd rows and of the per-point operands,
+// then the KB coefficients of the column (the complex layout is the larger, used for the fit check)
+template <bool CPLX>
+size_t row_smem_bytes(const sdft_ctx* c, int TY, int D, int NT) {
+    const size_t kv2 = CPLX ? 16 : 8;
+    return sizeof(float2) * (size_t)D * (TY + 2 * FD_RADIUS) * (c->n[0] + 2 * FD_RADIUS) +
+           (size_t)D * ((NT * (16 + 8 + 3 * 8 + 3 * kv2) + 15) & ~(size_t)15) +
+           sizeof(float2) * (size_t)std::max(1, c->natom);
+}
+
+// row-tile variant: usable when n1 is even, TY divides n2, the CTA has at most 512 threads and
+// the y halo fits ROW_HALO_UNITS_PER_THREAD 16-byte copies per thread
+template <int TY, int MAXT, int D>
+bool row_variant_ok(const sdft_ctx* c, int ncolE) {
+    const int n1 = c->n[0], n2 = c->n[1];
+    if (n1 % 2 || n2 % TY || n1 < 2 * FD_RADIUS) return false;
+    const int HX = n1 / 2, NT = HX * TY;
+    if (NT > MAXT || NT < 64) return false;
+    if (2 * FD_RADIUS * (HX + 6) > ROW_HALO_UNITS_PER_THREAD * NT) return false;
+    return row_smem_bytes<true>(c, TY, D, NT) <= 200 * 1024 && ncolE > 0;
+}
+
+// one launch of the row tile for one problem (grp null) or for nprob problems of a group (grp:
+// device table of RowProblem; kpt then only selects the shared grid quantities)
+template <bool CPLX, int TY, int PF, int MAXT, int MINB, int D>
+void launch_row_impl(sdft_ctx* c, int kpt, const float2* Y, const float2* Yprev, float2* Ynext, int ncolE,
+                     const float* V, const float2* kbC, double alpha, double beta, double shift, bool timed,
+                     int nprob, const RowProblem* grp, bool prev, bool haskb) {
+    SDFT_REQUIRE((row_variant_ok<TY, MAXT, D>(c, ncolE)), SDFT_ERR_INVALID_ARG, "row stencil variant does not fit");
+    const int n1 = c->n[0];
+    const int ytiles = c->n[1] / TY;
+    long long want = 6LL * 152;
+    int nzc = 1;
+    while ((long long)ytiles * ncolE * nprob * nzc < want && c->n[2] / (nzc + 1) >= 24) ++nzc;
+    const int zchunk = (c->n[2] + nzc - 1) / nzc;
+    nzc = (c->n[2] + zchunk - 1) / zchunk;
+    StepArgs<float> A = make_args<float>(c, kpt, alpha, beta, shift, zchunk, nzc);
+    SDFT_REQUIRE((long long)ncolE * nprob * nzc < 65536, SDFT_ERR_INVALID_ARG, "too many columns for one launch");
+    dim3 grid(ytiles, 1, (unsigned)(ncolE * nprob * nzc));
+    dim3 block(n1 / 2, TY);
+    const KBTables& kb = c->kb[kpt];
+    const size_t dsm = row_smem_bytes<CPLX>(c, TY, D, (n1 / 2) * TY);
+    ScopedTimer timer(timed ? c : nullptr, SDFT_K_STENCIL,
+                      (double)nprob * ncolE * (double)c->ng * sizeof(float2) * (prev ? 3.0 : 2.0));
+#define SDFT_ROW(P, KK)                                                                               \
+    do {                                                                                              \
+        auto kfn = cheb_row_kernel<CPLX, TY, PF, MAXT, MINB, D, P, KK, true>;                          \
+        SDFT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));  \
+        kfn<<<grid, block, dsm, c->stream>>>(Y, Yprev, Ynext, V, kbC, kb.patom, kb.pval32, kb.S, A, ncolE, grp); \
+    } while (0)
+    if (prev && haskb) SDFT_ROW(true, true);
+    else if (!prev && haskb) SDFT_ROW(false, true);
+    else if (prev && !haskb) SDFT_ROW(true, false);
+    else SDFT_ROW(false, false);
+#undef SDFT_ROW
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+template <bool CPLX, int TY, int PF, int MAXT, int MINB, int D>
+void launch_row_variant(sdft_ctx* c, int kpt, const float2* Y, const float2* Yprev, float2* Ynext, int ncolE,
+                        const float* V, const float2* kbC, double alpha, double beta, double shift, bool kin,
+                        bool timed) {
+    SDFT_REQUIRE(kin && V != nullptr, SDFT_ERR_INVALID_ARG, "row stencil variant needs V and the kinetic term");
+    const bool prev = Yprev != nullptr, haskb = kbC != nullptr && c->kb[kpt].S > 0;
+    launch_row_impl<CPLX, TY, PF, MAXT, MINB, D>(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, timed,
+                                                 1, nullptr, prev, haskb);
+}
+
+template <bool CPLX, int TY, int PF, int MAXT, int MINB, int D>
+void launch_row_group(sdft_ctx* c, int kpt, const RowProblem* grp, int nprob, int ncolE, bool prev, bool haskb) {
+    launch_row_impl<CPLX, TY, PF, MAXT, MINB, D>(c, kpt, nullptr, nullptr, nullptr, ncolE, nullptr, nullptr, 1.0,
+                                                 0.0, 0.0, true, nprob, grp, prev, haskb);
+}
+using GroupLauncher = void (*)(sdft_ctx*, int, const RowProblem*, int, int, bool, bool);
+
 template <typename E>
 using StepLauncher = void (*)(sdft_ctx*, int, const E*, const E*, E*, int, const typename Elem<E>::S*, const E*,
                               double, double, double, bool, bool);
+template <typename E>
+struct StepVariant {
+    StepLauncher<E> fn;
+    bool (*ok)(const sdft_ctx*, int);   // null: always usable
+    const char* name;
+    GroupLauncher group = nullptr;      // grouped launch over problems (row tiles only)
+};
 
 // Stencil tile autotuner: time every compiled variant on the real operands (Ynext is rewritten by
 // the chosen variant afterwards) and keep the fastest for this context.  SDFT_STENCIL_VARIANT=k
 // forces variant k.  Small problems use variant 0 without timing.
 template <typename E>
-int autotune_stencil(sdft_ctx* c, const StepLauncher<E>* table, int nvar, int kpt, const E* Y, const E* Yprev,
+int autotune_stencil(sdft_ctx* c, const StepVariant<E>* table, int nvar, int kpt, const E* Y, const E* Yprev,
                      E* Ynext, int ncolE, const typename Elem<E>::S* V, const E* kbC, double alpha, double beta,
                      double shift) {
+    auto usable = [&](int v) { return table[v].ok == nullptr || table[v].ok(c, ncolE); };
     if (const char* env = getenv("SDFT_STENCIL_VARIANT")) {
         const int v = atoi(env);
-        if (v >= 0 && v < nvar) return v;
+        if (v >= 0 && v < nvar && usable(v)) return v;
     }
-    if (nvar == 1 || (double)c->ng * ncolE < 4e6) return 0;
+    if (nvar == 1 || (double)c->ng * ncolE < 4e6 || V == nullptr) return -1;   // not tuned: caller uses 0
     cudaEvent_t a, b;
     SDFT_CUDA(cudaEventCreate(&a));
     SDFT_CUDA(cudaEventCreate(&b));
     int best = 0;
     float best_ms = 1e30f;
     for (int v = 0; v < nvar; ++v) {
-        table[v](c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, true, false);  // warm-up
+        if (!usable(v)) continue;
+        table[v].fn(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, true, false);  // warm-up
         SDFT_CUDA(cudaEventRecord(a, c->stream));
-        for (int r = 0; r < 3; ++r) table[v](c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, true, false);
+        for (int r = 0; r < 3; ++r)
+            table[v].fn(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, true, false);
         SDFT_CUDA(cudaEventRecord(b, c->stream));
         SDFT_CUDA(cudaEventSynchronize(b));
         float ms = 0.f;
@@ -553,8 +930,26 @@ int autotune_stencil(sdft_ctx* c, const StepLauncher<E>* table, int nvar, int kp
     return best;
 }
 
-
 }  // namespace
+
+template <typename E>
+void launch_project_group_impl(sdft_ctx* c, const KBProblem* grp, int nprob, int ncolE, bool cplx) {
+    const int natom = c->natom;
+    if (natom == 0 || ncolE == 0 || nprob == 0) return;
+    constexpr int NC = 4;
+    dim3 grid(natom, (ncolE + NC - 1) / NC, nprob);
+    ScopedTimer timer(c, SDFT_K_KB_PROJECT);
+    if (cplx) {
+        if constexpr (!std::is_same<E, double>::value)
+            kb_project_kernel<E, true, NC><<<grid, 256, 0, c->stream>>>(nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                       nullptr, 0, natom, ncolE, c->ng, grp);
+    } else {
+        kb_project_kernel<E, false, NC><<<grid, 256, 0, c->stream>>>(nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                    nullptr, 0, natom, ncolE, c->ng, grp);
+    }
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
 
 template <typename E>
 void launch_project_impl(sdft_ctx* c, int kpt, const E* Y, E* C, int ncolE) {
@@ -568,10 +963,10 @@ void launch_project_impl(sdft_ctx* c, int kpt, const E* Y, E* C, int ncolE) {
     if (kb.cplx) {
         if constexpr (!std::is_same<E, double>::value)
             kb_project_kernel<E, true, NC><<<grid, 256, 0, c->stream>>>(Y, C, kb.cnt, kb.idx, val, kb.gamma,
-                                                                       kb.cap, kb.natom, ncolE, c->ng);
+                                                                       kb.cap, kb.natom, ncolE, c->ng, nullptr);
     } else {
         kb_project_kernel<E, false, NC><<<grid, 256, 0, c->stream>>>(Y, C, kb.cnt, kb.idx, val, kb.gamma, kb.cap,
-                                                                    kb.natom, ncolE, c->ng);
+                                                                    kb.natom, ncolE, c->ng, nullptr);
     }
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);

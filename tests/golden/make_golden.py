@@ -23,6 +23,7 @@ from oracle import scf  # noqa: E402
 CELLS = {
     "two_atom_24": (workloads.two_atom_cell, dict(tol=1e-10, max_iter=300, final_tol=1e-10)),
     "lattice64_80": (workloads.lattice64_cell, dict(tol=1e-8, max_iter=150, final_tol=None)),
+    "kspin_20": (workloads.kspin_small_cell, dict(tol=1e-8, max_iter=300, final_tol=None)),
 }
 
 

@@ -77,16 +77,37 @@ def test_apply_h_matches_oracle(sd, precision, kred):
     assert _relerr(got, ref) < tol
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
-@pytest.mark.parametrize("kred", [(0.0, 0.0, 0.0), (0.25, 0.0, -0.5)])
-def test_every_stencil_tile_variant_matches_oracle(sd, variant, kred, monkeypatch):
-    # The autotuner may pick any compiled tile shape; each one must give the same H X.
+# FP32 tile variants compiled for each storage kind: (name, grid that the variant fits).
+# Row tiles need an even n1, TY | n2 and (n1/2)*TY threads in [64, max]; the grids below give
+# each row variant a shape it accepts (and several z chunks, ragged against the queue length).
+REAL_VARIANTS = [("col32x8", (9, 10, 11)), ("col32x8pf3", (9, 10, 11)), ("col32x16", (9, 10, 11)),
+                 ("col32x4", (9, 10, 11)), ("row4", (40, 40, 29)), ("row8", (40, 40, 29)),
+                 ("row5", (40, 40, 29)), ("row6", (24, 36, 31))]
+CPLX_VARIANTS = [("col32x8", (9, 10, 11)), ("col32x8pf3", (9, 10, 11)), ("row4", (40, 40, 29)),
+                 ("row8", (40, 40, 29)), ("row10", (40, 40, 29))]
+
+
+def _variant_cell(n):
+    c = workloads.small_cell(npts=10, L=4.0, natom=3, seed=21, nstates=6)
+    c.n = n
+    c.L = tuple(0.3 * k + 0.6 for k in n) if n[0] > 12 else (3.6, 4.0, 4.4)
+    rng = np.random.default_rng(5)
+    c.pos = rng.uniform(0, 1, (3, 3)) * np.array(c.L)
+    return c
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("variant", range(8))
+def test_every_stencil_tile_variant_matches_oracle(sd, variant, cplx, monkeypatch):
+    # The autotuner may pick any compiled tile shape; each one must give the same filter output.
     # 6 real states = 3 orbital pairs, so the two-column variants also run a ragged tail.
-    cplx = any(kred)
-    if cplx and variant > 1:
-        pytest.skip("complex blocks compile two variants")
+    table = CPLX_VARIANTS if cplx else REAL_VARIANTS
+    if variant >= len(table):
+        pytest.skip("no such variant for this storage kind")
+    name, n = table[variant]
+    kred = (0.25, 0.125, -0.5) if cplx else (0.0, 0.0, 0.0)
     monkeypatch.setenv("SDFT_STENCIL_VARIANT", str(variant))
-    cell = _ragged_cell()
+    cell = _variant_cell(n)
     ns = 6
     ctx = _ctx(sd, cell, sd.SDFT_MIXED, ns, kpts=[kred] if cplx else None)
     V = np.random.default_rng(11).normal(0, 0.4, cell.ngrid)
@@ -95,6 +116,7 @@ def test_every_stencil_tile_variant_matches_oracle(sd, variant, kred, monkeypatc
     x = sd.pack_block(X, sd.SDFT_MIXED)
     y = torch.empty_like(x)
     sd.sdft_chebyshev_filter(ctx, 0, 0, sd.SDFT_MIXED, x, y, ns, 4, 3.0, 90.0, -1.5)
+    assert sd.sdft_get_stencil_variant(ctx, cplx) == (variant, name)
     P = model.projectors(cell, kred)
     ref = chefsi.chebyshev_filter(lambda Z: ham.apply_h(cell, Z, V, P, model.kb_energies(cell), kred), X, 4,
                                   3.0, 90.0, -1.5)
@@ -308,3 +330,52 @@ def test_invalid_arguments_are_rejected(sd):
     with pytest.raises(sd.SdftError) as e:
         sd.sdft_set_veff(ctx, 0, bad)
     assert e.value.code == -7
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n", [1, 7, 24, 64, 65])
+def test_subspace_eig_matches_lapack(sd, n, cplx, monkeypatch):
+    """Generalized eigensolve Hs q = lambda M q: the one-CTA Jacobi solver (n <= 64) and cuSOLVER
+    (n = 65) against LAPACK, with M shaped like a filtered block's overlap (condition ~1e4)."""
+    import scipy.linalg as sla
+    rng = np.random.default_rng(n + 100 * cplx)
+    B = rng.normal(size=(3 * n, n)) * np.logspace(0, -2, n)
+    G = rng.normal(size=(3 * n, 3 * n))
+    if cplx:
+        B = B + 1j * rng.normal(size=(3 * n, n)) * np.logspace(0, -2, n)
+        G = G + 1j * rng.normal(size=(3 * n, 3 * n))
+    M = B.conj().T @ B
+    H = B.conj().T @ ((G + G.conj().T) / 2) @ B
+    lam_ref, Q_ref = sla.eigh(H, M)
+    cell = workloads.small_cell(npts=6, L=3.0, natom=1, seed=1, nstates=n + 1)
+    ctx = _ctx(sd, cell, sd.SDFT_FP64, n + 1, kpts=[(0.25, 0.0, 0.0)] if cplx else None)
+
+    def dev(A):
+        a = np.asfortranarray(A)
+        if cplx:
+            a = np.stack([a.real, a.imag], axis=-1)   # (n, n, 2) in Fortran order of (i, j)
+            return torch.from_numpy(np.ascontiguousarray(a.transpose(1, 0, 2))).cuda()
+        return torch.from_numpy(np.ascontiguousarray(A.T)).cuda()
+
+    m, h = dev(M), dev(H)
+    eig = torch.zeros(n, dtype=torch.float64, device="cuda")
+    sd.sdft_subspace_eig(ctx, cplx, m, h, eig, n)
+    lam = eig.cpu().numpy()
+    q = h.cpu().numpy()
+    Q = (q[..., 0] + 1j * q[..., 1]).T if cplx else q.T
+    scale = np.max(np.abs(lam_ref))
+    assert np.max(np.abs(lam - lam_ref)) < 1e-11 * scale
+    assert np.max(np.abs(Q.conj().T @ M @ Q - np.eye(n))) < 1e-10
+    assert np.max(np.abs(H @ Q - M @ Q * lam[None, :])) < 1e-9 * scale * np.max(np.abs(M))
+
+
+def test_subspace_eig_rejects_indefinite_overlap(sd):
+    cell = workloads.small_cell(npts=6, L=3.0, natom=1, seed=1, nstates=4)
+    ctx = _ctx(sd, cell, sd.SDFT_FP64, 4)
+    M = np.diag([1.0, -1.0, 2.0])
+    m = torch.from_numpy(M.copy()).cuda()
+    h = torch.from_numpy(np.eye(3)).cuda()
+    eig = torch.zeros(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(sd.SdftError) as e:
+        sd.sdft_subspace_eig(ctx, False, m, h, eig, 3)
+    assert e.value.code == -5
