@@ -146,6 +146,7 @@ struct sdft_ctx {
     bool timing = false;
     int stencil_choice[4] = {-1, -1, -1, -1};  // autotuned variant per storage kind
     int stencil_last[4] = {-1, -1, -1, -1};    // variant of the last launch per storage kind
+    int group_choice[2] = {-1, -1};            // autotuned row variant of grouped launches (real, complex)
     const char* stencil_last_name[4] = {nullptr, nullptr, nullptr, nullptr};
     bool aar_persistent = true;   // FP32 Poisson corrections in one cooperative launch
     bool test_barrier_extra = false;  // test hook: the persistent barrier waits for one CTA too many
@@ -322,6 +323,7 @@ int group_variant_f32(sdft_ctx* c, bool cplx, int ncolE);
 void launch_group_step_f32(sdft_ctx* c, bool cplx, int variant, const RowProblem* grp, int nprob, int ncolE,
                            bool prev, bool haskb);
 void launch_group_project_f32(sdft_ctx* c, bool cplx, const KBProblem* grp, int nprob, int ncolE);
+int autotune_group_f32(sdft_ctx* c, bool cplx, const RowProblem* grp, int nprob, int ncolE, bool haskb);
 
 // ---- batched.cu ----------------------------------------------------------------------
 bool batched_eig_supported(int n);

@@ -412,6 +412,14 @@ static void chefsi_pass_group(sdft_ctx* c, const std::vector<Problem*>& G, int v
                               c->stream));
     SDFT_CUDA(cudaMemcpyAsync(c->g_ktab, c->g_ktab_h.data(), sizeof(KBProblem) * ntab, cudaMemcpyHostToDevice,
                               c->stream));
+    // first grouped pass of this context: time the row tiles on the H Y launch (its output buffer
+    // is rewritten below), keep the fastest
+    int& gch = c->group_choice[cplx ? 1 : 0];
+    if (gch < 0) {
+        if (haskb) launch_group_project_f32(c, cplx, c->g_ktab + (size_t)m * np, np, ncolE);
+        gch = autotune_group_f32(c, cplx, c->g_rtab + (size_t)m * np, np, ncolE, haskb);
+    }
+    if (gch >= 0) variant = gch;
     // filter (m steps) and H Y, every problem per launch
     for (int k = 0; k <= m; ++k) {
         if (haskb) launch_group_project_f32(c, cplx, c->g_ktab + (size_t)k * np, np, ncolE);

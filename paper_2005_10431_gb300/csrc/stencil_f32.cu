@@ -23,9 +23,9 @@ const StepVariant<float2> kReal[] = {
 const StepVariant<float2> kCplx[] = {
     {&launch_variant<float2, true, 32, 8, 2, 2, 4>, nullptr, "col32x8"},
     {&launch_variant<float2, true, 32, 8, 3, 2, 3>, nullptr, "col32x8pf3"},
-    {&launch_row_variant<true, 4, 1, 256, 1, 3>, &row_ok<4, 256, 3>, "row4", &launch_row_group<true, 4, 1, 256, 1, 3>},
-    {&launch_row_variant<true, 8, 1, 256, 1, 3>, &row_ok<8, 256, 3>, "row8", &launch_row_group<true, 8, 1, 256, 1, 3>},
-    {&launch_row_variant<true, 10, 2, 256, 1, 3>, &row_ok<10, 256, 3>, "row10", &launch_row_group<true, 10, 2, 256, 1, 3>},
+    {&launch_row_variant<true, 4, 1, 256, 2, 3>, &row_ok<4, 256, 3>, "row4", &launch_row_group<true, 4, 1, 256, 2, 3>},
+    {&launch_row_variant<true, 8, 1, 256, 2, 3>, &row_ok<8, 256, 3>, "row8", &launch_row_group<true, 8, 1, 256, 2, 3>},
+    {&launch_row_variant<true, 10, 1, 256, 2, 3>, &row_ok<10, 256, 3>, "row10", &launch_row_group<true, 10, 1, 256, 2, 3>},
 };
 constexpr int kNReal = sizeof(kReal) / sizeof(kReal[0]);
 constexpr int kNCplx = sizeof(kCplx) / sizeof(kCplx[0]);
@@ -76,6 +76,39 @@ int group_variant_f32(sdft_ctx* c, bool cplx, int ncolE) {
     for (int v = 0; v < nvar; ++v)
         if (table[v].group && table[v].ok(c, ncolE)) return v;
     return -1;
+}
+
+// time every fitting row variant on one grouped launch (tab: a table whose Ynext may be
+// overwritten) and return the fastest
+int autotune_group_f32(sdft_ctx* c, bool cplx, const RowProblem* grp, int nprob, int ncolE, bool haskb) {
+    const StepVariant<float2>* table = cplx ? kCplx : kReal;
+    const int nvar = cplx ? kNCplx : kNReal;
+    if (const char* env = getenv("SDFT_STENCIL_VARIANT")) {
+        const int v = atoi(env);
+        if (v >= 0 && v < nvar && table[v].group && table[v].ok(c, ncolE)) return v;
+    }
+    cudaEvent_t a, b;
+    SDFT_CUDA(cudaEventCreate(&a));
+    SDFT_CUDA(cudaEventCreate(&b));
+    int best = -1;
+    float best_ms = 1e30f;
+    for (int v = 0; v < nvar; ++v) {
+        if (!table[v].group || !table[v].ok(c, ncolE)) continue;
+        table[v].group(c, 0, grp, nprob, ncolE, false, haskb);   // warm-up
+        SDFT_CUDA(cudaEventRecord(a, c->stream));
+        for (int r = 0; r < 2; ++r) table[v].group(c, 0, grp, nprob, ncolE, false, haskb);
+        SDFT_CUDA(cudaEventRecord(b, c->stream));
+        SDFT_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        SDFT_CUDA(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
 }
 
 void launch_group_step_f32(sdft_ctx* c, bool cplx, int variant, const RowProblem* grp, int nprob, int ncolE,

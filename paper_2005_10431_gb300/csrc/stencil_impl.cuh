@@ -386,6 +386,8 @@ cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __rest
 // staged by cp.async 16-byte copies in a D-stage ring; z-neighbours come from a register queue
 // of 16-byte vectors.  Per-point operands (V, KB slots, Yprev) are read straight from L2.
 constexpr int ROW_HALO_UNITS_PER_THREAD = 4;
+constexpr int ROW_X0 = 16;   // shared-row entry of x = 0 (128 bytes of float2)
+__host__ __device__ inline int row_stride(int n1) { return ((ROW_X0 + n1 + FD_RADIUS) + 15) / 16 * 16; }
 
 
 template <bool CPLX, int TY, int PF, int MAXT, int MINB, int D, bool PREV, bool KB, bool VLOC>
@@ -432,7 +434,10 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
     constexpr int K = ROW_HALO_UNITS_PER_THREAD;
     const int HX = blockDim.x;                 // n1 / 2
     const int n1 = A.n1;
-    const int RS = n1 + 2 * R;                 // shared row stride (float2), even
+    // shared row: point x at entry ROW_X0 + x (128-byte aligned for x = 0), left pad (x = -6..-1)
+    // just below, right pad (x = n1..n1+5) just above; the stride is a multiple of 128 bytes, so
+    // every 16-byte y-neighbour read of a quarter-warp is one aligned 128-byte wavefront
+    const int RS = row_stride(n1);
     const int SE = (TY + 2 * R) * RS;          // one stage (float2)
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int NT = HX * TY, tid = ty * HX + tx;
@@ -465,34 +470,29 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
         for (int i = tid; i < A.natom; i += NT) Cs[i] = C[(long long)col * A.natom + i];
 
     // y-halo units (two points each): 12 rows x (HX interior + 3 left-pad + 3 right-pad)
+    // hdst: shared entry; complex blocks keep the unit's wrap code (tx+1) | (ty+1) << 2 in bits 24..27
     int hdst[K], hsrc[K];
-    float2 hph[K];
     const int upr = HX + 6;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int u = tid + k * NT;
         hdst[k] = -1;
         hsrc[k] = 0;
-        hph[k] = make_float2(1.f, 0.f);
         if (u < 2 * R * upr) {
             const int hr = u / upr, j = u - hr * upr;
             const int trow = hr < R ? hr : TY + hr;          // tile row
             int tyw;
             const int wy = wrapi(y0 - R + trow, A.n2, tyw);
             int x, entry, txw = 0;
-            if (j < HX) { x = 2 * j; entry = R + 2 * j; }
-            else if (j < HX + 3) { x = n1 - R + 2 * (j - HX); entry = 2 * (j - HX); txw = -1; }
-            else { x = 2 * (j - HX - 3); entry = n1 + R + 2 * (j - HX - 3); txw = 1; }
+            if (j < HX) { x = 2 * j; entry = ROW_X0 + 2 * j; }
+            else if (j < HX + 3) { x = n1 - R + 2 * (j - HX); entry = ROW_X0 - R + 2 * (j - HX); txw = -1; }
+            else { x = 2 * (j - HX - 3); entry = ROW_X0 + n1 + 2 * (j - HX - 3); txw = 1; }
             hdst[k] = trow * RS + entry;
             hsrc[k] = wy * n1 + x;
-            if constexpr (CPLX) {
-                float2 ph = make_float2(1.f, 0.f);
-                if (txw) ph = apply_phase<float2, float>(ph, txw, phr[0], phi[0]);
-                if (tyw) ph = apply_phase<float2, float>(ph, tyw, phr[1], phi[1]);
-                hph[k] = ph;
-            }
+            if constexpr (CPLX) hdst[k] |= ((txw + 1) | ((tyw + 1) << 2)) << 24;
         }
     }
+    constexpr int HMASK = CPLX ? 0xFFFFFF : -1;
     float2 phxp = make_float2(1.f, 0.f), phxm = make_float2(1.f, 0.f);   // x wrap +1 / -1
     if constexpr (CPLX) {
         phxp = make_float2(phr[0], phi[0]);
@@ -507,7 +507,7 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
             const float2* src = Yc + off;
 #pragma unroll
             for (int k = 0; k < K; ++k)
-                if (hdst[k] >= 0) cp_async<16>(T + hdst[k], src + hsrc[k]);
+                if (hdst[k] >= 0) cp_async<16>(T + (hdst[k] & HMASK), src + hsrc[k]);
             const long long g = off + gxy;
             if (PREV) cp_async<16>(op_prev(st), Pc + g);
             if (VLOC) cp_async<8>(op_v(st), V + g);
@@ -546,7 +546,7 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
 #pragma unroll
     for (int d = 0; d < D - 1; ++d) issue(z0 + d, d);
 
-    const int own = (R + ty) * RS + R + gx;   // this thread's first point in a stage
+    const int own = (R + ty) * RS + ROW_X0 + gx;   // this thread's first point in a stage
     for (int zb = z0; zb < z1; zb += QN) {
 #pragma unroll
         for (int ph = 0; ph < QN; ++ph) {
@@ -560,11 +560,16 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
                 if (tx >= HX - 3) *reinterpret_cast<float4*>(T + own - n1) = CPLX ? cm(cen, phxm) : cen;
                 if constexpr (CPLX) {
 #pragma unroll
-                    for (int k = 0; k < K; ++k)
-                        if (hdst[k] >= 0 && (hph[k].x != 1.f || hph[k].y != 0.f)) {
-                            float4* p = reinterpret_cast<float4*>(T + hdst[k]);
-                            *p = cm(*p, hph[k]);
+                    for (int k = 0; k < K; ++k) {
+                        const int code = hdst[k] >> 24;
+                        if (hdst[k] >= 0 && code != 5) {   // 5: no wrap in x or y
+                            const int txw = (code & 3) - 1, tyw = (code >> 2) - 1;
+                            float2 ph = txw > 0 ? phxp : (txw < 0 ? phxm : make_float2(1.f, 0.f));
+                            if (tyw) ph = cmul(ph, make_float2(phr[1], tyw > 0 ? phi[1] : -phi[1]));
+                            float4* p = reinterpret_cast<float4*>(T + (hdst[k] & HMASK));
+                            *p = cm(*p, ph);
                         }
+                    }
                 }
                 {
                     float4 v = ld4(Yc + zq.off + gxy);
@@ -810,7 +815,7 @@ void launch_variant(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, 
 template <bool CPLX>
 size_t row_smem_bytes(const sdft_ctx* c, int TY, int D, int NT) {
     const size_t kv2 = CPLX ? 16 : 8;
-    return sizeof(float2) * (size_t)D * (TY + 2 * FD_RADIUS) * (c->n[0] + 2 * FD_RADIUS) +
+    return sizeof(float2) * (size_t)D * (TY + 2 * FD_RADIUS) * row_stride(c->n[0]) +
            (size_t)D * ((NT * (16 + 8 + 3 * 8 + 3 * kv2) + 15) & ~(size_t)15) +
            sizeof(float2) * (size_t)std::max(1, c->natom);
 }

@@ -4,6 +4,9 @@ of displaced 8-atom cells, then starts the SCF of held-out cells of the same seq
 
 Checked: the learned guess is much closer to the converged density than the superposition of
 atomic densities, the SCF from it needs fewer iterations, and it converges to the same energy.
+The SCF of these cells is limited by how fast the filter converges the random starting orbitals,
+so the start density pays off when the first SCF iteration (at the V_eff of that density) runs
+more filter passes: both starts use 12 passes there.
 """
 import numpy as np
 import pytest
@@ -25,10 +28,10 @@ def sd():
     return m
 
 
-def _ctx(sd, cell):
+def _ctx(sd, cell, passes=4):
     return sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species,
                           dict(nstates=cell.nstates, cheb_degree=cell.cheb_degree, precision=sd.SDFT_MIXED,
-                               scf_tol=1e-6, max_scf=150, seed=cell.seed))
+                               scf_tol=1e-6, max_scf=150, seed=cell.seed, first_scf_filter_passes=passes))
 
 
 def _iters_to(log, e_ref, tol):
@@ -65,11 +68,11 @@ def test_learned_guess_cuts_scf_iterations(sd):
     gain = []
     for seed in range(2000, 2004):
         cell = workloads.qmd_lattice8_cell(seed)
-        c0 = _ctx(sd, cell)
+        c0 = _ctx(sd, cell, passes=12)
         r0 = sd.sdft_scf(c0)
         rho_star = sd.sdft_get_density(c0).sum(axis=0)
         sad = sd.sdft_get_sad_density(c0)
-        c1 = _ctx(sd, cell)
+        c1 = _ctx(sd, cell, passes=12)
         sd.sdft_mlp_predict(c1, p)
         r1 = sd.sdft_scf(c1)
         assert r0["converged"] and r1["converged"]
@@ -89,5 +92,5 @@ def test_learned_guess_cuts_scf_iterations(sd):
         rho0 *= cell.nelec / (rho0.sum() * dV)
         assert np.abs(rho0 - rho_star).sum() < 0.2 * np.abs(sad - rho_star).sum()
     gain = np.array(gain)
-    assert gain[:, 1].mean() < gain[:, 0].mean()      # fewer iterations to the SCF tolerance
-    assert gain[:, 3].mean() <= gain[:, 2].mean()     # and no later to 1e-5 Ha/atom
+    assert gain[:, 1].mean() < gain[:, 0].mean() - 1.0    # fewer iterations to the SCF tolerance
+    assert gain[:, 3].mean() < gain[:, 2].mean()          # and sooner within 1e-5 Ha/atom
