@@ -55,9 +55,10 @@ def cell_for(name):
 
 
 def golden(name):
+    """The oracle's converged reference for the workload (tests/golden/make_golden.py), or None."""
     path = os.path.join(ROOT, "tests", "golden", name + ".json")
     if not os.path.exists(path):
-        raise SystemExit(f"missing oracle reference {path} (tests/golden/make_golden.py {name})")
+        return None
     return json.load(open(path))
 
 
@@ -176,16 +177,19 @@ def oracle_sample(name, budget_s):
         if time.time() - t_start > budget_s or len(times) >= 3:
             break
     t_hx = min(times)
-    hist = g["history"]
-    e_ref = g["energy"]
     i_hit = None
-    for rec in hist:
-        ok = abs(rec["energy"] - e_ref) / cell.natom <= TOL_PER_ATOM
-        if ok and i_hit is None:
-            i_hit = rec["iter"]
-        elif not ok:
-            i_hit = None
-    passes = 4 + (i_hit if i_hit is not None else len(hist))
+    if g is not None:
+        hist = g["history"]
+        e_ref = g["energy"]
+        for rec in hist:
+            ok = abs(rec["energy"] - e_ref) / cell.natom <= TOL_PER_ATOM
+            if ok and i_hit is None:
+                i_hit = rec["iter"]
+            elif not ok:
+                i_hit = None
+        passes = 4 + (i_hit if i_hit is not None else len(hist))
+    else:
+        passes = 4 + 40   # no oracle run recorded: an assumed 40 SCF iterations
     n_hx = passes * (cell.cheb_degree + 1)
     threads = os.cpu_count() or 1
     return {"value": t_hx * n_hx, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -195,6 +199,14 @@ def oracle_sample(name, budget_s):
 
 
 # ---------------------------------------------------------------------------------------
+def max_over_ranks(dist, vals, device):
+    """Element-wise maximum of a list of floats over all ranks (the slowest replica sets the time)."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -223,7 +235,8 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     cell = cell_for(args.workload)
     g = golden(args.workload)
-    e_ref = g["energy"]
+    # without the oracle's converged energy the time-to-tolerance cannot be measured (value null)
+    e_ref = g["energy"] if g else float("nan")
     prec = sd.SDFT_MIXED if args.precision == "mixed" else sd.SDFT_FP64
     opts = dict(nstates=cell.nstates, cheb_degree=cell.cheb_degree, precision=prec, scf_tol=cell.scf_tol,
                 max_scf=200, final_fp64_pass=1 if prec == sd.SDFT_MIXED else 0, kT=cell.kT, seed=cell.seed)
@@ -271,9 +284,7 @@ def run_ours(args, rank, world, dist):
     value = statistics.mean(ok_hits) if len(ok_hits) == len(hits) else float("nan")
     ms_per_step = 1e3 * elapsed / args.steps
     if dist:
-        t = torch.tensor([value if value == value else 1e30, ms_per_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        value, ms_per_step = float(t[0]), float(t[1])
+        value, ms_per_step = max_over_ranks(dist, [value if value == value else 1e30, ms_per_step], "cuda")
     # roofline of the dominant kernel (stencil + Chebyshev step)
     st = stats["stencil"]
     peak, peak_kind = measured_peaks()
@@ -338,7 +349,10 @@ def run_ours(args, rank, world, dist):
         "fp64_gpu": fp64,
         "learned_guess": False,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if g is None:
+        out["value"] = None
+        out["reference"] = f"oracle reference tests/golden/{args.workload}.json missing"
+    if rank == 0 and not args.no_cpu_baseline and g is not None:
         out["cpu_baseline"] = oracle_sample(args.workload, args.cpu_sample_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
