@@ -39,6 +39,16 @@ __device__ __forceinline__ float2 eadd(float2 a, float2 b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
     return u2f(r);
 }
+// acc + s * a with the scalar kept as a plain operand (two FP32 FMAs): for coefficients that live
+// in the constant bank this avoids building the broadcast register pair of the packed form
+__device__ __forceinline__ float2 efmas(float s, float2 a, float2 acc) {
+    return make_float2(fmaf(s, a.x, acc.x), fmaf(s, a.y, acc.y));
+}
+__device__ __forceinline__ double efmas(double s, double a, double acc) { return fma(s, a, acc); }
+__device__ __forceinline__ float efmas(float s, float a, float acc) { return fmaf(s, a, acc); }
+__device__ __forceinline__ double2 efmas(double s, double2 a, double2 acc) {
+    return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y));
+}
 __device__ __forceinline__ double efma(double s, double a, double acc) { return fma(s, a, acc); }
 __device__ __forceinline__ float efma(float s, float a, float acc) { return fmaf(s, a, acc); }
 __device__ __forceinline__ float eadd(float a, float b) { return a + b; }
@@ -74,6 +84,7 @@ struct StepArgs {
     S c0, alpha, beta, shift;
     S phr[3], phi[3];           // Bloch phase exp(2 pi i kappa_d) per axis
     int n1, n2, n3, zchunk, nzc, natom;
+    int iso;                    // 1: cx == cy == cz (cubic grid spacing)
     long long ng;
 };
 
@@ -386,8 +397,10 @@ cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __rest
 // staged by cp.async 16-byte copies in a D-stage ring; z-neighbours come from a register queue
 // of 16-byte vectors.  Per-point operands (V, KB slots, Yprev) are read straight from L2.
 constexpr int ROW_HALO_UNITS_PER_THREAD = 4;
-constexpr int ROW_X0 = 16;   // shared-row entry of x = 0 (128 bytes of float2)
-__host__ __device__ inline int row_stride(int n1) { return ((ROW_X0 + n1 + FD_RADIUS) + 15) / 16 * 16; }
+constexpr int ROW_X0 = FD_RADIUS;   // shared-row entry of x = 0 (after the 6-point left pad)
+// shared row stride (float2): left pad, n1 points, right pad; even, so 16-byte reads stay aligned
+// (a 128-byte aligned layout measured slower: its extra padding cost one resident CTA per SM)
+__host__ __device__ inline int row_stride(int n1) { return n1 + 2 * FD_RADIUS; }
 
 
 template <bool CPLX, int TY, int PF, int MAXT, int MINB, int D, bool PREV, bool KB, bool VLOC>
@@ -434,9 +447,8 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
     constexpr int K = ROW_HALO_UNITS_PER_THREAD;
     const int HX = blockDim.x;                 // n1 / 2
     const int n1 = A.n1;
-    // shared row: point x at entry ROW_X0 + x (128-byte aligned for x = 0), left pad (x = -6..-1)
-    // just below, right pad (x = n1..n1+5) just above; the stride is a multiple of 128 bytes, so
-    // every 16-byte y-neighbour read of a quarter-warp is one aligned 128-byte wavefront
+    // shared row: point x at entry ROW_X0 + x, left pad (x = -6..-1) just below, right pad
+    // (x = n1..n1+5) just above
     const int RS = row_stride(n1);
     const int SE = (TY + 2 * R) * RS;          // one stage (float2)
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -583,41 +595,65 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
                 issue(z + D - 1, (z - z0 + D - 1) % D);
 
                 const float2 c0 = make_float2(cen.x, cen.y), c1 = make_float2(cen.z, cen.w);
-                float2 a0 = efma(A.c0, c0, ezero<float2>());
-                float2 a1 = efma(A.c0, c1, ezero<float2>());
-                {   // x: six 16-byte reads cover x-6 .. x+7
+                float2 a0 = efmas(A.c0, c0, ezero<float2>());
+                float2 a1 = efmas(A.c0, c1, ezero<float2>());
+                {   // x: six 16-byte reads cover x-6 .. x+7 of the pair
                     const float4 L0 = ld4(T + own - 6), L1 = ld4(T + own - 4), L2 = ld4(T + own - 2);
                     const float4 R0 = ld4(T + own + 2), R1 = ld4(T + own + 4), R2 = ld4(T + own + 6);
 #define LO(v) make_float2(v.x, v.y)
 #define HI(v) make_float2(v.z, v.w)
-                    a0 = efma(A.cx[1], eadd(HI(L2), c1), a0);
-                    a0 = efma(A.cx[2], eadd(LO(L2), LO(R0)), a0);
-                    a0 = efma(A.cx[3], eadd(HI(L1), HI(R0)), a0);
-                    a0 = efma(A.cx[4], eadd(LO(L1), LO(R1)), a0);
-                    a0 = efma(A.cx[5], eadd(HI(L0), HI(R1)), a0);
-                    a0 = efma(A.cx[6], eadd(LO(L0), LO(R2)), a0);
-                    a1 = efma(A.cx[1], eadd(c0, LO(R0)), a1);
-                    a1 = efma(A.cx[2], eadd(HI(L2), HI(R0)), a1);
-                    a1 = efma(A.cx[3], eadd(LO(L2), LO(R1)), a1);
-                    a1 = efma(A.cx[4], eadd(HI(L1), HI(R1)), a1);
-                    a1 = efma(A.cx[5], eadd(LO(L1), LO(R2)), a1);
-                    a1 = efma(A.cx[6], eadd(HI(L0), HI(R2)), a1);
-                }
+                    // x pair sums of point 0 (x = 2tx) and point 1 (x = 2tx + 1) at distance r
+                    auto sx0 = [&](int r) {
+                        switch (r) {
+                            case 1: return eadd(HI(L2), c1);
+                            case 2: return eadd(LO(L2), LO(R0));
+                            case 3: return eadd(HI(L1), HI(R0));
+                            case 4: return eadd(LO(L1), LO(R1));
+                            case 5: return eadd(HI(L0), HI(R1));
+                            default: return eadd(LO(L0), LO(R2));
+                        }
+                    };
+                    auto sx1 = [&](int r) {
+                        switch (r) {
+                            case 1: return eadd(c0, LO(R0));
+                            case 2: return eadd(HI(L2), HI(R0));
+                            case 3: return eadd(LO(L2), LO(R1));
+                            case 4: return eadd(HI(L1), HI(R1));
+                            case 5: return eadd(LO(L1), LO(R2));
+                            default: return eadd(HI(L0), HI(R2));
+                        }
+                    };
+                    if (A.iso) {
+                        // one coefficient per distance: add the x, y and z pair sums first
 #pragma unroll
-                for (int r = 1; r <= R; ++r) {
-                    const float4 up = ld4(T + own - r * RS), dn = ld4(T + own + r * RS);
-                    const float4 zu = q[(ph + R + r) % QN], zd = q[(ph + R - r + QN) % QN];
-                    a0 = efma(A.cy[r], eadd(LO(up), LO(dn)), a0);
-                    a1 = efma(A.cy[r], eadd(HI(up), HI(dn)), a1);
-                    a0 = efma(A.cz[r], eadd(LO(zu), LO(zd)), a0);
-                    a1 = efma(A.cz[r], eadd(HI(zu), HI(zd)), a1);
+                        for (int r = 1; r <= R; ++r) {
+                            const float4 up = ld4(T + own - r * RS), dn = ld4(T + own + r * RS);
+                            const float4 zu = q[(ph + R + r) % QN], zd = q[(ph + R - r + QN) % QN];
+                            const float2 t0 = eadd(eadd(sx0(r), eadd(LO(up), LO(dn))), eadd(LO(zu), LO(zd)));
+                            const float2 t1 = eadd(eadd(sx1(r), eadd(HI(up), HI(dn))), eadd(HI(zu), HI(zd)));
+                            a0 = efmas(A.cx[r], t0, a0);
+                            a1 = efmas(A.cx[r], t1, a1);
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 1; r <= R; ++r) {
+                            const float4 up = ld4(T + own - r * RS), dn = ld4(T + own + r * RS);
+                            const float4 zu = q[(ph + R + r) % QN], zd = q[(ph + R - r + QN) % QN];
+                            a0 = efmas(A.cx[r], sx0(r), a0);
+                            a1 = efmas(A.cx[r], sx1(r), a1);
+                            a0 = efmas(A.cy[r], eadd(LO(up), LO(dn)), a0);
+                            a1 = efmas(A.cy[r], eadd(HI(up), HI(dn)), a1);
+                            a0 = efmas(A.cz[r], eadd(LO(zu), LO(zd)), a0);
+                            a1 = efmas(A.cz[r], eadd(HI(zu), HI(zd)), a1);
+                        }
+                    }
                 }
                 const long long g = (long long)z * plane + gxy;
                 const int st = (z - z0) % D;
                 if (VLOC) {
                     const float2 v = *op_v(st);
-                    a0 = efma(v.x, c0, a0);
-                    a1 = efma(v.y, c1, a1);
+                    a0 = efmas(v.x, c0, a0);
+                    a1 = efmas(v.y, c1, a1);
                 }
                 if (KB) {
                     auto kb_add = [&](int2 at, KV2 kv) {
@@ -625,8 +661,8 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
                             if (at.x >= 0) a0 = eadd(a0, cmul(LO(kv), Cs[at.x]));
                             if (at.y >= 0) a1 = eadd(a1, cmul(HI(kv), Cs[at.y]));
                         } else {
-                            if (at.x >= 0) a0 = efma(kv.x, Cs[at.x], a0);
-                            if (at.y >= 0) a1 = efma(kv.y, Cs[at.y], a1);
+                            if (at.x >= 0) a0 = efmas(kv.x, Cs[at.x], a0);
+                            if (at.y >= 0) a1 = efmas(kv.y, Cs[at.y], a1);
                         }
                     };
 #pragma unroll
@@ -638,13 +674,16 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
                         kb_add(at, __ldg(reinterpret_cast<const KV2*>(reinterpret_cast<const KV*>(pval) + k * A.ng + g)));
                     }
                 }
-                float2 o0 = efma(alpha, efma(-shift, c0, a0), ezero<float2>());
-                float2 o1 = efma(alpha, efma(-shift, c1, a1), ezero<float2>());
+                // out = alpha (acc - shift center) - beta prev
+                float2 o0 = efmas(-shift, c0, a0), o1 = efmas(-shift, c1, a1);
                 if (PREV) {
                     const float4 pv = *op_prev(st);
-                    o0 = efma(-beta, LO(pv), o0);
-                    o1 = efma(-beta, HI(pv), o1);
+                    const float rb = beta / alpha;
+                    o0 = efmas(-rb, LO(pv), o0);
+                    o1 = efmas(-rb, HI(pv), o1);
                 }
+                o0 = make_float2(alpha * o0.x, alpha * o0.y);
+                o1 = make_float2(alpha * o1.x, alpha * o1.y);
                 *reinterpret_cast<float4*>(Ynext + (long long)col * A.ng + g) = make_float4(o0.x, o0.y, o1.x, o1.y);
 #undef LO
 #undef HI
@@ -751,6 +790,9 @@ StepArgs<S> make_args(sdft_ctx* c, int kpt, double alpha, double beta, double sh
         A.phr[d] = (S)cos(2.0 * M_PI * kd);
         A.phi[d] = (S)sin(2.0 * M_PI * kd);
     }
+    A.iso = 1;
+    for (int r = 0; r <= FD_RADIUS; ++r)
+        if (c->coef.cx[r] != c->coef.cy[r] || c->coef.cx[r] != c->coef.cz[r]) A.iso = 0;
     A.n1 = c->n[0];
     A.n2 = c->n[1];
     A.n3 = c->n[2];
