@@ -15,6 +15,9 @@ const StepVariant<float2> kReal[] = {
     {&launch_variant<float2, false, 32, 8, 3, 2, 3>, nullptr, "col32x8pf3"},
     {&launch_variant<float2, false, 32, 16, 2, 1, 3>, nullptr, "col32x16"},
     {&launch_variant<float2, false, 32, 4, 2, 4, 4>, nullptr, "col32x4"},
+    {&launch_variant<float2, false, 32, 8, 2, 3, 3>, nullptr, "col32x8occ3"},
+    {&launch_variant<float2, false, 32, 8, 2, 4, 3>, nullptr, "col32x8occ4"},
+    {&launch_variant<float2, false, 32, 4, 2, 6, 3>, nullptr, "col32x4occ6"},
     {&launch_row_variant<false, 4, 1, 256, 2, 3>, &row_ok<4, 256, 3>, "row4", &launch_row_group<false, 4, 1, 256, 2, 3>},
     {&launch_row_variant<false, 8, 1, 512, 1, 3>, &row_ok<8, 512, 3>, "row8", &launch_row_group<false, 8, 1, 512, 1, 3>},
     {&launch_row_variant<false, 5, 2, 320, 1, 3>, &row_ok<5, 320, 3>, "row5", &launch_row_group<false, 5, 2, 320, 1, 3>},

@@ -81,7 +81,8 @@ def test_apply_h_matches_oracle(sd, precision, kred):
 # Row tiles need an even n1, TY | n2 and (n1/2)*TY threads in [64, max]; the grids below give
 # each row variant a shape it accepts (and several z chunks, ragged against the queue length).
 REAL_VARIANTS = [("col32x8", (9, 10, 11)), ("col32x8pf3", (9, 10, 11)), ("col32x16", (9, 10, 11)),
-                 ("col32x4", (9, 10, 11)), ("row4", (40, 40, 29)), ("row8", (40, 40, 29)),
+                 ("col32x4", (9, 10, 11)), ("col32x8occ3", (9, 10, 11)), ("col32x8occ4", (9, 10, 11)),
+                 ("col32x4occ6", (9, 10, 11)), ("row4", (40, 40, 29)), ("row8", (40, 40, 29)),
                  ("row5", (40, 40, 29)), ("row6", (24, 36, 31))]
 CPLX_VARIANTS = [("col32x8", (9, 10, 11)), ("col32x8pf3", (9, 10, 11)), ("row4", (40, 40, 29)),
                  ("row8", (40, 40, 29)), ("row10", (40, 40, 29))]
@@ -97,7 +98,7 @@ def _variant_cell(n):
 
 
 @pytest.mark.parametrize("cplx", [False, True])
-@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("variant", range(11))
 def test_every_stencil_tile_variant_matches_oracle(sd, variant, cplx, monkeypatch):
     # The autotuner may pick any compiled tile shape; each one must give the same filter output.
     # 6 real states = 3 orbital pairs, so the two-column variants also run a ragged tail.
