@@ -39,16 +39,6 @@ __device__ __forceinline__ float2 eadd(float2 a, float2 b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
     return u2f(r);
 }
-// acc + s * a with the scalar kept as a plain operand (two FP32 FMAs): for coefficients that live
-// in the constant bank this avoids building the broadcast register pair of the packed form
-__device__ __forceinline__ float2 efmas(float s, float2 a, float2 acc) {
-    return make_float2(fmaf(s, a.x, acc.x), fmaf(s, a.y, acc.y));
-}
-__device__ __forceinline__ double efmas(double s, double a, double acc) { return fma(s, a, acc); }
-__device__ __forceinline__ float efmas(float s, float a, float acc) { return fmaf(s, a, acc); }
-__device__ __forceinline__ double2 efmas(double s, double2 a, double2 acc) {
-    return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y));
-}
 __device__ __forceinline__ double efma(double s, double a, double acc) { return fma(s, a, acc); }
 __device__ __forceinline__ float efma(float s, float a, float acc) { return fmaf(s, a, acc); }
 __device__ __forceinline__ float eadd(float a, float b) { return a + b; }
@@ -84,7 +74,6 @@ struct StepArgs {
     S c0, alpha, beta, shift;
     S phr[3], phi[3];           // Bloch phase exp(2 pi i kappa_d) per axis
     int n1, n2, n3, zchunk, nzc, natom;
-    int iso;                    // 1: cx == cy == cz (cubic grid spacing)
     long long ng;
 };
 
@@ -346,13 +335,15 @@ cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __rest
                     const long long g = (long long)z * plane + gxy;
                     E acc = ezero<E>();
                     if (KIN) {
-                        acc = efma(A.c0, center, acc);
+                        // three independent chains (z, x, y) instead of one 19-deep FMA chain
+                        E az = efma(A.c0, center, ezero<E>()), ax = ezero<E>(), ay = ezero<E>();
 #pragma unroll
                         for (int r = 1; r <= R; ++r) {
-                            acc = efma(A.cz[r], eadd(q[(ph + R + r) % QN], q[(ph + R - r + QN) % QN]), acc);
-                            acc = efma(A.cx[r], eadd(S_.tile[R + ty][R + tx + r], S_.tile[R + ty][R + tx - r]), acc);
-                            acc = efma(A.cy[r], eadd(S_.tile[R + ty + r][R + tx], S_.tile[R + ty - r][R + tx]), acc);
+                            az = efma(A.cz[r], eadd(q[(ph + R + r) % QN], q[(ph + R - r + QN) % QN]), az);
+                            ax = efma(A.cx[r], eadd(S_.tile[R + ty][R + tx + r], S_.tile[R + ty][R + tx - r]), ax);
+                            ay = efma(A.cy[r], eadd(S_.tile[R + ty + r][R + tx], S_.tile[R + ty - r][R + tx]), ay);
                         }
+                        acc = eadd(az, eadd(ax, ay));
                     }
                     if (VLOC) acc = efma(S_.v[ty][tx], center, acc);
                     if (KB) {
@@ -595,65 +586,44 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
                 issue(z + D - 1, (z - z0 + D - 1) % D);
 
                 const float2 c0 = make_float2(cen.x, cen.y), c1 = make_float2(cen.z, cen.w);
-                float2 a0 = efmas(A.c0, c0, ezero<float2>());
-                float2 a1 = efmas(A.c0, c1, ezero<float2>());
+                // per point three independent accumulation chains (x, y, z) instead of one
+                float2 a0 = efma(A.c0, c0, ezero<float2>()), a1 = efma(A.c0, c1, ezero<float2>());
+                float2 b0 = ezero<float2>(), b1 = ezero<float2>(), d0 = ezero<float2>(), d1 = ezero<float2>();
                 {   // x: six 16-byte reads cover x-6 .. x+7 of the pair
                     const float4 L0 = ld4(T + own - 6), L1 = ld4(T + own - 4), L2 = ld4(T + own - 2);
                     const float4 R0 = ld4(T + own + 2), R1 = ld4(T + own + 4), R2 = ld4(T + own + 6);
 #define LO(v) make_float2(v.x, v.y)
 #define HI(v) make_float2(v.z, v.w)
-                    // x pair sums of point 0 (x = 2tx) and point 1 (x = 2tx + 1) at distance r
-                    auto sx0 = [&](int r) {
-                        switch (r) {
-                            case 1: return eadd(HI(L2), c1);
-                            case 2: return eadd(LO(L2), LO(R0));
-                            case 3: return eadd(HI(L1), HI(R0));
-                            case 4: return eadd(LO(L1), LO(R1));
-                            case 5: return eadd(HI(L0), HI(R1));
-                            default: return eadd(LO(L0), LO(R2));
-                        }
-                    };
-                    auto sx1 = [&](int r) {
-                        switch (r) {
-                            case 1: return eadd(c0, LO(R0));
-                            case 2: return eadd(HI(L2), HI(R0));
-                            case 3: return eadd(LO(L2), LO(R1));
-                            case 4: return eadd(HI(L1), HI(R1));
-                            case 5: return eadd(LO(L1), LO(R2));
-                            default: return eadd(HI(L0), HI(R2));
-                        }
-                    };
-                    if (A.iso) {
-                        // one coefficient per distance: add the x, y and z pair sums first
-#pragma unroll
-                        for (int r = 1; r <= R; ++r) {
-                            const float4 up = ld4(T + own - r * RS), dn = ld4(T + own + r * RS);
-                            const float4 zu = q[(ph + R + r) % QN], zd = q[(ph + R - r + QN) % QN];
-                            const float2 t0 = eadd(eadd(sx0(r), eadd(LO(up), LO(dn))), eadd(LO(zu), LO(zd)));
-                            const float2 t1 = eadd(eadd(sx1(r), eadd(HI(up), HI(dn))), eadd(HI(zu), HI(zd)));
-                            a0 = efmas(A.cx[r], t0, a0);
-                            a1 = efmas(A.cx[r], t1, a1);
-                        }
-                    } else {
-#pragma unroll
-                        for (int r = 1; r <= R; ++r) {
-                            const float4 up = ld4(T + own - r * RS), dn = ld4(T + own + r * RS);
-                            const float4 zu = q[(ph + R + r) % QN], zd = q[(ph + R - r + QN) % QN];
-                            a0 = efmas(A.cx[r], sx0(r), a0);
-                            a1 = efmas(A.cx[r], sx1(r), a1);
-                            a0 = efmas(A.cy[r], eadd(LO(up), LO(dn)), a0);
-                            a1 = efmas(A.cy[r], eadd(HI(up), HI(dn)), a1);
-                            a0 = efmas(A.cz[r], eadd(LO(zu), LO(zd)), a0);
-                            a1 = efmas(A.cz[r], eadd(HI(zu), HI(zd)), a1);
-                        }
-                    }
+                    a0 = efma(A.cx[1], eadd(HI(L2), c1), a0);
+                    a0 = efma(A.cx[2], eadd(LO(L2), LO(R0)), a0);
+                    a0 = efma(A.cx[3], eadd(HI(L1), HI(R0)), a0);
+                    a0 = efma(A.cx[4], eadd(LO(L1), LO(R1)), a0);
+                    a0 = efma(A.cx[5], eadd(HI(L0), HI(R1)), a0);
+                    a0 = efma(A.cx[6], eadd(LO(L0), LO(R2)), a0);
+                    a1 = efma(A.cx[1], eadd(c0, LO(R0)), a1);
+                    a1 = efma(A.cx[2], eadd(HI(L2), HI(R0)), a1);
+                    a1 = efma(A.cx[3], eadd(LO(L2), LO(R1)), a1);
+                    a1 = efma(A.cx[4], eadd(HI(L1), HI(R1)), a1);
+                    a1 = efma(A.cx[5], eadd(LO(L1), LO(R2)), a1);
+                    a1 = efma(A.cx[6], eadd(HI(L0), HI(R2)), a1);
                 }
+#pragma unroll
+                for (int r = 1; r <= R; ++r) {
+                    const float4 up = ld4(T + own - r * RS), dn = ld4(T + own + r * RS);
+                    const float4 zu = q[(ph + R + r) % QN], zd = q[(ph + R - r + QN) % QN];
+                    b0 = efma(A.cy[r], eadd(LO(up), LO(dn)), b0);
+                    b1 = efma(A.cy[r], eadd(HI(up), HI(dn)), b1);
+                    d0 = efma(A.cz[r], eadd(LO(zu), LO(zd)), d0);
+                    d1 = efma(A.cz[r], eadd(HI(zu), HI(zd)), d1);
+                }
+                a0 = eadd(a0, eadd(b0, d0));
+                a1 = eadd(a1, eadd(b1, d1));
                 const long long g = (long long)z * plane + gxy;
                 const int st = (z - z0) % D;
                 if (VLOC) {
                     const float2 v = *op_v(st);
-                    a0 = efmas(v.x, c0, a0);
-                    a1 = efmas(v.y, c1, a1);
+                    a0 = efma(v.x, c0, a0);
+                    a1 = efma(v.y, c1, a1);
                 }
                 if (KB) {
                     auto kb_add = [&](int2 at, KV2 kv) {
@@ -661,8 +631,8 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
                             if (at.x >= 0) a0 = eadd(a0, cmul(LO(kv), Cs[at.x]));
                             if (at.y >= 0) a1 = eadd(a1, cmul(HI(kv), Cs[at.y]));
                         } else {
-                            if (at.x >= 0) a0 = efmas(kv.x, Cs[at.x], a0);
-                            if (at.y >= 0) a1 = efmas(kv.y, Cs[at.y], a1);
+                            if (at.x >= 0) a0 = efma(kv.x, Cs[at.x], a0);
+                            if (at.y >= 0) a1 = efma(kv.y, Cs[at.y], a1);
                         }
                     };
 #pragma unroll
@@ -675,15 +645,13 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
                     }
                 }
                 // out = alpha (acc - shift center) - beta prev
-                float2 o0 = efmas(-shift, c0, a0), o1 = efmas(-shift, c1, a1);
+                float2 o0 = efma(alpha, efma(-shift, c0, a0), ezero<float2>());
+                float2 o1 = efma(alpha, efma(-shift, c1, a1), ezero<float2>());
                 if (PREV) {
                     const float4 pv = *op_prev(st);
-                    const float rb = beta / alpha;
-                    o0 = efmas(-rb, LO(pv), o0);
-                    o1 = efmas(-rb, HI(pv), o1);
+                    o0 = efma(-beta, LO(pv), o0);
+                    o1 = efma(-beta, HI(pv), o1);
                 }
-                o0 = make_float2(alpha * o0.x, alpha * o0.y);
-                o1 = make_float2(alpha * o1.x, alpha * o1.y);
                 *reinterpret_cast<float4*>(Ynext + (long long)col * A.ng + g) = make_float4(o0.x, o0.y, o1.x, o1.y);
 #undef LO
 #undef HI
@@ -790,9 +758,6 @@ StepArgs<S> make_args(sdft_ctx* c, int kpt, double alpha, double beta, double sh
         A.phr[d] = (S)cos(2.0 * M_PI * kd);
         A.phi[d] = (S)sin(2.0 * M_PI * kd);
     }
-    A.iso = 1;
-    for (int r = 0; r <= FD_RADIUS; ++r)
-        if (c->coef.cx[r] != c->coef.cy[r] || c->coef.cx[r] != c->coef.cz[r]) A.iso = 0;
     A.n1 = c->n[0];
     A.n2 = c->n[1];
     A.n3 = c->n[2];
