@@ -110,6 +110,9 @@ typedef struct {
     int batch_problems;        /* 1: SDFT_MIXED runs the CheFSI passes of all (spin, k) problems of one
                                   storage kind together (grouped stencil / KB launches, batched
                                   eigensolve); 0: one problem after another */
+    int use_graphs;            /* 1: the grouped filter of a batched pass (table upload, m KB projections
+                                  and stencil steps, and the H Y of Rayleigh-Ritz) is captured once as a
+                                  CUDA graph and replayed every pass (not while kernel timing is on) */
 } sdft_options;
 
 /* Per-iteration record of the SCF (paper Sec. 2.1 ".out" progress). */

@@ -51,7 +51,7 @@ class sdft_options(C.Structure):
         ("pulay_period", C.c_int), ("pulay_restart", C.c_int), ("scf_tol", C.c_double), ("max_scf", C.c_int),
         ("precision", C.c_int), ("final_fp64_pass", C.c_int), ("poisson_tol", C.c_double),
         ("init_guess", C.c_int), ("initial_moment", C.c_double), ("seed", C.c_uint64),
-        ("batch_problems", C.c_int),
+        ("batch_problems", C.c_int), ("use_graphs", C.c_int),
     ]
 
 

@@ -44,6 +44,18 @@ void ctx_free_all(sdft_ctx* c) {
         cudaFreeHost(c->hscal);
         c->hscal = nullptr;
     }
+    if (c->g_graph) {
+        cudaGraphExecDestroy(c->g_graph);
+        c->g_graph = nullptr;
+    }
+    if (c->cap_stream) {
+        cudaStreamDestroy(c->cap_stream);
+        c->cap_stream = nullptr;
+    }
+    if (c->g_rtab_pin) cudaFreeHost(c->g_rtab_pin);
+    if (c->g_ktab_pin) cudaFreeHost(c->g_ktab_pin);
+    c->g_rtab_pin = nullptr;
+    c->g_ktab_pin = nullptr;
 }
 
 static cudaEvent_t take_event(sdft_ctx* c) {
@@ -292,6 +304,7 @@ void sdft_default_options(sdft_options* o) {
     o->initial_moment = 0.125;
     o->seed = 0;
     o->batch_problems = 1;
+    o->use_graphs = 1;
 }
 
 sdft_status sdft_create(const sdft_cell* cell, const sdft_grid* grid, const sdft_atoms* atoms, int ntypes,

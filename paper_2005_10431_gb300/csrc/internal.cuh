@@ -211,6 +211,14 @@ struct sdft_ctx {
     int g_tab_cap = 0;
     std::vector<sdft::RowProblem> g_rtab_h;
     std::vector<sdft::KBProblem> g_ktab_h;
+    // pinned copies of the step tables (sources of the graph's upload) and the captured filter
+    sdft::RowProblem* g_rtab_pin = nullptr;
+    sdft::KBProblem* g_ktab_pin = nullptr;
+    int g_pin_cap = 0;
+    cudaGraphExec_t g_graph = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    std::vector<long long> g_graph_key;
+    int g_graph_launches = 0;
 
     // results
     std::vector<sdft_iter_record> log;

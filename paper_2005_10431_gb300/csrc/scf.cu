@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 
 namespace sdft {
 
@@ -408,22 +409,80 @@ static void chefsi_pass_group(sdft_ctx* c, const std::vector<Problem*>& G, int v
         kp.Y = r.Y;
         c->g_ktab_h[m * np + p] = kp;
     }
-    SDFT_CUDA(cudaMemcpyAsync(c->g_rtab, c->g_rtab_h.data(), sizeof(RowProblem) * ntab, cudaMemcpyHostToDevice,
-                              c->stream));
-    SDFT_CUDA(cudaMemcpyAsync(c->g_ktab, c->g_ktab_h.data(), sizeof(KBProblem) * ntab, cudaMemcpyHostToDevice,
-                              c->stream));
     // first grouped pass of this context: time the row tiles on the H Y launch (its output buffer
     // is rewritten below), keep the fastest
     int& gch = c->group_choice[cplx ? 1 : 0];
     if (gch < 0) {
+        SDFT_CUDA(cudaMemcpyAsync(c->g_rtab, c->g_rtab_h.data(), sizeof(RowProblem) * ntab, cudaMemcpyHostToDevice,
+                                  c->stream));
+        SDFT_CUDA(cudaMemcpyAsync(c->g_ktab, c->g_ktab_h.data(), sizeof(KBProblem) * ntab, cudaMemcpyHostToDevice,
+                                  c->stream));
         if (haskb) launch_group_project_f32(c, cplx, c->g_ktab + (size_t)m * np, np, ncolE);
         gch = autotune_group_f32(c, cplx, c->g_rtab + (size_t)m * np, np, ncolE, haskb);
     }
     if (gch >= 0) variant = gch;
-    // filter (m steps) and H Y, every problem per launch
-    for (int k = 0; k <= m; ++k) {
-        if (haskb) launch_group_project_f32(c, cplx, c->g_ktab + (size_t)k * np, np, ncolE);
-        launch_group_step_f32(c, cplx, variant, c->g_rtab + (size_t)k * np, np, ncolE, k > 0 && k < m, haskb);
+    // the filter (m steps) and H Y, every problem per launch, after uploading this pass's tables
+    auto enqueue = [&](const RowProblem* rsrc, const KBProblem* ksrc) {
+        SDFT_CUDA(cudaMemcpyAsync(c->g_rtab, rsrc, sizeof(RowProblem) * ntab, cudaMemcpyHostToDevice, c->stream));
+        SDFT_CUDA(cudaMemcpyAsync(c->g_ktab, ksrc, sizeof(KBProblem) * ntab, cudaMemcpyHostToDevice, c->stream));
+        for (int k = 0; k <= m; ++k) {
+            if (haskb) launch_group_project_f32(c, cplx, c->g_ktab + (size_t)k * np, np, ncolE);
+            launch_group_step_f32(c, cplx, variant, c->g_rtab + (size_t)k * np, np, ncolE, k > 0 && k < m, haskb);
+        }
+    };
+    if (c->opt.use_graphs && !c->timing) {
+        // CUDA graph of the grouped filter: captured once, replayed every pass; the replay copies
+        // this pass's coefficients from the pinned tables, so only the host copy below changes
+        if (c->g_pin_cap < ntab) {
+            if (c->g_rtab_pin) cudaFreeHost(c->g_rtab_pin);
+            if (c->g_ktab_pin) cudaFreeHost(c->g_ktab_pin);
+            c->g_rtab_pin = nullptr;
+            c->g_ktab_pin = nullptr;
+            SDFT_CUDA(cudaMallocHost((void**)&c->g_rtab_pin, sizeof(RowProblem) * ntab));
+            SDFT_CUDA(cudaMallocHost((void**)&c->g_ktab_pin, sizeof(KBProblem) * ntab));
+            c->g_pin_cap = ntab;
+            if (c->g_graph) cudaGraphExecDestroy(c->g_graph);
+            c->g_graph = nullptr;
+        }
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));   // the previous replay has read the pinned tables
+        std::memcpy(c->g_rtab_pin, c->g_rtab_h.data(), sizeof(RowProblem) * ntab);
+        std::memcpy(c->g_ktab_pin, c->g_ktab_h.data(), sizeof(KBProblem) * ntab);
+        // a graph bakes in the launch shapes and the block pointers; recapture when they change
+        std::vector<long long> key = {np, variant, (long long)cplx, m, (long long)haskb, ncolE};
+        for (int p = 0; p < np; ++p) key.push_back((long long)(uintptr_t)G[p]->X);
+        if (!c->g_graph || key != c->g_graph_key) {
+            if (c->g_graph) cudaGraphExecDestroy(c->g_graph);
+            c->g_graph = nullptr;
+            const uint64_t l0 = c->launches;
+            cudaGraph_t graph = nullptr;
+            // capture on a private stream (the context's stream may be the legacy default stream,
+            // which cannot be captured); the graph is then launched on the context's stream
+            if (!c->cap_stream) SDFT_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+            cudaStream_t user_stream = c->stream;
+            c->stream = c->cap_stream;
+            SDFT_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            try {
+                enqueue(c->g_rtab_pin, c->g_ktab_pin);
+            } catch (...) {
+                cudaStreamEndCapture(c->stream, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                c->stream = user_stream;
+                throw;
+            }
+            const cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+            c->stream = user_stream;
+            SDFT_CUDA(ce);
+            const cudaError_t ie = cudaGraphInstantiate(&c->g_graph, graph, 0);
+            cudaGraphDestroy(graph);
+            SDFT_CUDA(ie);
+            c->g_graph_launches = (int)(c->launches - l0);
+            c->launches = l0;
+            c->g_graph_key = key;
+        }
+        SDFT_CUDA(cudaGraphLaunch(c->g_graph, c->stream));
+        count_launch(c, c->g_graph_launches);
+    } else {
+        enqueue(c->g_rtab_h.data(), c->g_ktab_h.data());
     }
     // Gram matrices per problem, one batched eigensolve, rotations per problem
     for (int p = 0; p < np; ++p) {

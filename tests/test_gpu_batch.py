@@ -30,11 +30,11 @@ def _gold(name):
     return json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name + ".json")))
 
 
-def _run(sd, cell, batch, tol):
+def _run(sd, cell, batch, tol, graphs=1, max_scf=200):
     ctx = sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species,
                          dict(nstates=cell.nstates, cheb_degree=cell.cheb_degree, precision=sd.SDFT_MIXED,
-                              scf_tol=tol, max_scf=200, nspin=cell.nspin, kT=cell.kT, seed=cell.seed,
-                              batch_problems=batch),
+                              scf_tol=tol, max_scf=max_scf, nspin=cell.nspin, kT=cell.kT, seed=cell.seed,
+                              batch_problems=batch, use_graphs=graphs),
                          kpts=cell.kpts, kw=cell.kw)
     n0 = sd.sdft_launch_count(ctx)
     r = sd.sdft_scf(ctx)
@@ -57,3 +57,17 @@ def test_batched_chefsi_matches_problem_by_problem_and_oracle(sd):
     assert np.max(np.abs(eb[:, :, :nocc] - np.array(ref["eigs"])[:, :, :nocc])) < 1e-5
     # fewer launches per SCF iteration than one problem at a time
     assert lb / rb["niter"] < 0.5 * ls / rs["niter"]
+
+
+def test_graph_replay_of_the_grouped_filter_is_exact(sd):
+    """The CUDA graph replays the same launches with the same tables: the SCF history is bitwise the
+    one of the directly launched batched filter."""
+    cell = workloads.kspin_small_cell()
+    cg, rg, lg = _run(sd, cell, 1, 1e-12, graphs=1, max_scf=8)
+    cd, rd, ld = _run(sd, cell, 1, 1e-12, graphs=0, max_scf=8)
+    eg = [r["energy"] for r in sd.sdft_get_scf_log(cg)]
+    ed = [r["energy"] for r in sd.sdft_get_scf_log(cd)]
+    assert len(eg) == len(ed) == 8
+    assert eg == ed
+    assert np.array_equal(sd.sdft_get_density(cg), sd.sdft_get_density(cd))
+    assert lg == ld      # replayed graph launches are counted like direct ones
