@@ -207,6 +207,17 @@ sdft_status sdft_chebyshev_filter(sdft_ctx* ctx, int spin, int kpt, int precisio
 sdft_status sdft_rayleigh_ritz(sdft_ctx* ctx, int spin, int kpt, int precision,
                                const void* y, void* x, double* eig, int ncol);
 
+/* Chebyshev filter of several independent cells at once (the paper's filter, Sec. 2.1, applied to
+ * n cells of different grids and sizes): cell i is the context ctxs[i] (SDFT_MIXED, Gamma point,
+ * spin 0 V_eff as set for it), x[i] -> y[i] its FP32 paired block of nstates columns (device),
+ * degree m with the cell's own bounds a0[i] < a[i] < b[i] (host arrays).  Each Chebyshev step is
+ * ONE column-tile stencil launch over all cells (per-cell grid, coefficients and recurrence scalars
+ * in a constant-memory table) after the cells' KB projections; every cell computes exactly what
+ * sdft_chebyshev_filter computes for it with the column tile.  1 <= n <= 64; all contexts must use
+ * the same CUDA stream.  Returns after the work is enqueued and completed (synchronises). */
+sdft_status sdft_chebyshev_filter_multi(sdft_ctx* const* ctxs, int n, const void* const* x, void* const* y,
+                                        int degree, const double* a, const double* b, const double* a0);
+
 /* Subspace matrices only: M = Y^H Y and Hs = Y^H (H Y) as FP64 ncol x ncol (device,
  * column-major; complex problems write double2).  hy is the device block H Y. */
 sdft_status sdft_subspace_matrices(sdft_ctx* ctx, int kpt, int precision, const void* y,

@@ -20,7 +20,7 @@ __all__ = [
     "sdft_scf", "sdft_reset", "sdft_get_eigenvalues", "sdft_get_occupations", "sdft_get_density",
     "sdft_set_density", "sdft_get_forces", "sdft_get_scf_log", "sdft_get_pseudocharge", "sdft_get_sad_density",
     "sdft_set_orbitals", "sdft_get_orbitals", "sdft_set_veff", "sdft_apply_h", "sdft_chebyshev_filter",
-    "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_subspace_matrices_noalloc", "sdft_subspace_eig", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
+    "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_subspace_matrices_noalloc", "sdft_subspace_eig", "sdft_chebyshev_filter_multi", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
     "sdft_lanczos_bounds", "sdft_launch_count", "sdft_get_stencil_variant", "sdft_set_timing", "sdft_get_kernel_stats",
     "sdft_reset_kernel_stats", "pack_block", "unpack_block", "block_shape",
     "SDFT_MLP_NFEAT", "SDFT_MLP_NPARAM", "sdft_mlp_dataset", "sdft_mlp_loss_grad", "sdft_mlp_adam",
@@ -267,6 +267,18 @@ def sdft_subspace_matrices_noalloc(precision: int, is_complex: bool, y, hy, ngri
     _check(_lib.lib().sdft_subspace_matrices_noalloc(precision, 1 if is_complex else 0, _ptr(y), _ptr(hy), ngrid,
                                                      ncol, _ptr(m), _ptr(hs), C.c_void_p(s)), None)
     return m, hs
+
+
+def sdft_chebyshev_filter_multi(ctxs, xs, ys, degree: int, a, b, a0):
+    """One filter of degree `degree` on several cells (contexts) with one stencil launch per step."""
+    n = len(ctxs)
+    P = C.c_void_p * n
+    D = C.c_double * n
+    hv = [c.handle.value if hasattr(c.handle, "value") else c.handle for c in ctxs]
+    _check(_lib.lib().sdft_chebyshev_filter_multi(P(*hv), n, P(*[_ptr(x) for x in xs]),
+                                                  P(*[_ptr(y) for y in ys]), degree, D(*a), D(*b), D(*a0)),
+           ctxs[0].handle)
+    return ys
 
 
 def sdft_subspace_eig(ctx: Context, is_complex: bool, m, hs, eig, ncol: int):

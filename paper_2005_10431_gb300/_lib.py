@@ -120,6 +120,9 @@ SIGNATURES = {
     "sdft_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "sdft_get_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(sdft_kernel_stats)]),
     "sdft_reset_kernel_stats": (C.c_int, [C.c_void_p]),
+    "sdft_chebyshev_filter_multi": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p),
+                                              C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_double),
+                                              C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "sdft_subspace_eig": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "sdft_get_stencil_variant": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_char_p, C.c_size_t]),
     "sdft_mlp_dataset": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),

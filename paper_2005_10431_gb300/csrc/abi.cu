@@ -711,6 +711,30 @@ sdft_status sdft_reset_kernel_stats(sdft_ctx* c) {
     })
 }
 
+sdft_status sdft_chebyshev_filter_multi(sdft_ctx* const* ctxs, int n, const void* const* x, void* const* y,
+                                        int degree, const double* a, const double* b, const double* a0) {
+    if (!ctxs || n < 1 || !ctxs[0]) return SDFT_ERR_INVALID_ARG;
+    sdft_ctx* c0 = ctxs[0];
+    SDFT_TRY(c0, {
+        SDFT_REQUIRE(n <= 64 && x && y && a && b && a0, SDFT_ERR_INVALID_ARG, "need 1..64 cells and all arrays");
+        std::vector<sdft_ctx*> cs(n);
+        std::vector<const void*> xs(n);
+        std::vector<void*> ys(n);
+        for (int i = 0; i < n; ++i) {
+            sdft_ctx* c = ctxs[i];
+            SDFT_REQUIRE(c != nullptr && x[i] && y[i] && x[i] != y[i], SDFT_ERR_INVALID_ARG, "null context or block");
+            SDFT_REQUIRE(c->stream == c0->stream, SDFT_ERR_INVALID_ARG, "all contexts must share one stream");
+            SDFT_REQUIRE(c->opt.precision == SDFT_MIXED && !c->kb[0].cplx, SDFT_ERR_INVALID_ARG,
+                         "multi-cell filter takes SDFT_MIXED Gamma-point contexts");
+            cs[i] = c;
+            xs[i] = x[i];
+            ys[i] = y[i];
+        }
+        sdft::chebyshev_filter_multi(cs, xs, ys, degree, a, b, a0);
+        SDFT_CUDA(cudaStreamSynchronize(c0->stream));
+    })
+}
+
 sdft_status sdft_subspace_eig(sdft_ctx* c, int is_complex, double* m, double* hs, double* eig, int ncol) {
     SDFT_TRY(c, {
         SDFT_REQUIRE(m && hs && eig, SDFT_ERR_INVALID_ARG, "null pointer");

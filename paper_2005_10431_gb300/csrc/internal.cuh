@@ -332,6 +332,11 @@ void launch_group_step_f32(sdft_ctx* c, bool cplx, int variant, const RowProblem
                            bool prev, bool haskb);
 void launch_group_project_f32(sdft_ctx* c, bool cplx, const KBProblem* grp, int nprob, int ncolE);
 int autotune_group_f32(sdft_ctx* c, bool cplx, const RowProblem* grp, int nprob, int ncolE, bool haskb);
+// Chebyshev filter of the FP32 real blocks of several cells (contexts with their own grids) with
+// one column-tile stencil launch per step (scf.cu; kernels in stencil_f32.cu)
+void chebyshev_filter_multi(const std::vector<sdft_ctx*>& ctxs, const std::vector<const void*>& X,
+                            const std::vector<void*>& Y, int degree, const double* a, const double* b,
+                            const double* a0);
 
 // ---- batched.cu ----------------------------------------------------------------------
 bool batched_eig_supported(int n);

@@ -2,6 +2,9 @@
 // for FP32 blocks (two lanes per element: an orbital pair, or re/im of a Bloch orbital).
 #include "stencil_impl.cuh"
 
+#include <array>
+#include <vector>
+
 namespace sdft {
 namespace {
 // variants timed by the autotuner.  Column tiles: (TX, TY, queue prefetch PF, min blocks per SM,
@@ -120,6 +123,115 @@ void launch_group_step_f32(sdft_ctx* c, bool cplx, int variant, const RowProblem
     c->stencil_last[cplx ? 1 : 0] = variant;
     c->stencil_last_name[cplx ? 1 : 0] = table[variant].name;
     table[variant].group(c, 0, grp, nprob, ncolE, prev, haskb);
+}
+
+// One column-tile launch over several cells (each its own context, grid and block); probs[i].A
+// carries cell i's recurrence step.  All contexts share the stream of the first one.
+void launch_multi_step_f32(const std::vector<sdft_ctx*>& ctxs, std::vector<MultiProblem>& probs, bool prev) {
+    constexpr int TX = 32, TY = 8, PF = 2, MINB = 2, D = 4;
+    const int n = (int)probs.size();
+    SDFT_REQUIRE(n >= 1 && n <= MULTI_MAX, SDFT_ERR_INVALID_ARG, "multi-cell launch takes 1..64 cells");
+    sdft_ctx* c0 = ctxs[0];
+    long long total = 0;
+    int max_natom = 1;
+    double bytes = 0;
+    for (int i = 0; i < n; ++i) {
+        MultiProblem& P = probs[i];
+        const sdft_ctx* c = ctxs[i];
+        P.tiles_x = (c->n[0] + TX - 1) / TX;
+        P.tiles_y = (c->n[1] + TY - 1) / TY;
+        P.cta_begin = (int)total;
+        total += (long long)P.tiles_x * P.tiles_y * (c->opt.nstates / 2) * P.A.nzc;
+        P.cta_end = (int)total;
+        max_natom = std::max(max_natom, c->natom);
+        bytes += (double)(c->opt.nstates / 2) * (double)c->ng * sizeof(float2) * (prev ? 3.0 : 2.0);
+    }
+    SDFT_REQUIRE(total < (1LL << 31), SDFT_ERR_INVALID_ARG, "multi-cell launch too large");
+    SDFT_CUDA(cudaMemcpyToSymbolAsync(c_multi, probs.data(), sizeof(MultiProblem) * n, 0, cudaMemcpyHostToDevice,
+                                      c0->stream));
+    const size_t dsm = sizeof(Stage<float2, float, float, TX, TY, 3>) * D + sizeof(float2) * (size_t)max_natom;
+    ScopedTimer timer(c0, SDFT_K_STENCIL, bytes);
+    auto launch = [&](auto kfn) {
+        if (dsm > 48 * 1024)
+            SDFT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+        kfn<<<(unsigned)total, dim3(TX, TY), dsm, c0->stream>>>(n);
+    };
+    if (prev) launch(cheb_multi_kernel<TX, TY, PF, MINB, D, true>);
+    else launch(cheb_multi_kernel<TX, TY, PF, MINB, D, false>);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c0);
+}
+
+// z chunks of one cell inside a multi-cell launch: at least 16 planes per chunk, enough CTAs overall
+int multi_nzc(const sdft_ctx* c, long long ctas_other) {
+    const long long want = 8LL * 152;
+    const long long base = (long long)((c->n[0] + 31) / 32) * ((c->n[1] + 7) / 8) * (c->opt.nstates / 2);
+    int nzc = 1;
+    while (ctas_other + base * nzc < want && c->n[2] / (nzc + 1) >= 16) ++nzc;
+    return nzc;
+}
+
+StepArgs<float> multi_args(sdft_ctx* c, double alpha, double beta, double shift, int nzc) {
+    const int zchunk = (c->n[2] + nzc - 1) / nzc;
+    return make_args<float>(c, 0, alpha, beta, shift, zchunk, (c->n[2] + zchunk - 1) / zchunk);
+}
+
+void chebyshev_filter_multi(const std::vector<sdft_ctx*>& ctxs, const std::vector<const void*>& X,
+                            const std::vector<void*>& Y, int m, const double* a, const double* b, const double* a0) {
+    const int n = (int)ctxs.size();
+    SDFT_REQUIRE(m >= 1, SDFT_ERR_INVALID_ARG, "degree must be >= 1");
+    // per cell: the recurrence scalars and a ring of its own block buffers (T1, T2, Y)
+    std::vector<double> e(n), cc(n), sigma1(n), sigma(n);
+    std::vector<std::array<float2*, 3>> ring(n);
+    long long ctas = 0;
+    std::vector<int> nzc(n);
+    for (int i = 0; i < n; ++i) {
+        sdft_ctx* c = ctxs[i];
+        SDFT_REQUIRE(b[i] > a[i] && a[i] > a0[i], SDFT_ERR_INVALID_ARG, "filter bounds must satisfy a0 < a < b");
+        e[i] = 0.5 * (b[i] - a[i]);
+        cc[i] = 0.5 * (b[i] + a[i]);
+        sigma1[i] = sigma[i] = e[i] / (a0[i] - cc[i]);
+        float2* t[2];
+        int got = 0;
+        for (int k = 0; k < 4 && got < 2; ++k)
+            if (c->blk[k] != X[i] && c->blk[k] != Y[i]) t[got++] = (float2*)c->blk[k];
+        SDFT_REQUIRE(got == 2, SDFT_ERR_INVALID_ARG, "no free block buffers for the filter");
+        ring[i] = {t[0], t[1], (float2*)Y[i]};
+        nzc[i] = multi_nzc(c, ctas);
+        ctas += (long long)((c->n[0] + 31) / 32) * ((c->n[1] + 7) / 8) * (c->opt.nstates / 2) * nzc[i];
+    }
+    auto slot = [&](int i, int k) -> float2* { return ring[i][(((2 - (m - k)) % 3) + 3) % 3]; };
+    std::vector<MultiProblem> probs(n);
+    for (int k = 1; k <= m; ++k) {
+        for (int i = 0; i < n; ++i) {
+            sdft_ctx* c = ctxs[i];
+            const int ncolE = c->opt.nstates / 2;
+            const float2* cur = k == 1 ? (const float2*)X[i] : slot(i, k - 1);
+            const float2* prv = k == 1 ? nullptr : (k == 2 ? (const float2*)X[i] : slot(i, k - 2));
+            const bool kb = c->kb[0].S > 0;
+            if (kb) launch_kb_project<float2>(c, 0, cur, (float2*)c->C32, ncolE);
+            double alpha, beta = 0.0;
+            if (k == 1) {
+                alpha = sigma1[i] / e[i];
+            } else {
+                const double s2 = 1.0 / (2.0 / sigma1[i] - sigma[i]);
+                alpha = 2.0 * s2 / e[i];
+                beta = sigma[i] * s2;
+                sigma[i] = s2;
+            }
+            MultiProblem& P = probs[i];
+            P.A = multi_args(c, alpha, beta, cc[i], nzc[i]);
+            P.Y = cur;
+            P.Yprev = prv;
+            P.Ynext = slot(i, k);
+            P.V = c->veff32;
+            P.C = (const float2*)c->C32;
+            P.patom = c->kb[0].patom;
+            P.pval = c->kb[0].pval32;
+            P.nslot = kb ? c->kb[0].S : 0;
+        }
+        launch_multi_step_f32(ctxs, probs, k > 1);
+    }
 }
 
 void launch_group_project_f32(sdft_ctx* c, bool cplx, const KBProblem* grp, int nprob, int ncolE) {

@@ -210,12 +210,13 @@ struct Stage {
 // One CTA: TX x TY grid columns, planes [z0, z1), one element-column (orbital pair / Bloch
 // orbital).  z-neighbours: register queue, loaded PF planes ahead.  x/y halo and per-point
 // operands: D-stage cp.async ring, issued D-1 planes ahead, one __syncthreads per plane.
-template <typename E, bool CPLX, int TX, int TY, int PF, int MINB, int D, bool PREV, bool KB, bool VLOC, bool KIN>
-__global__ void __launch_bounds__(TX * TY, MINB)
-cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __restrict__ Ynext,
-                 const typename Elem<E>::S* __restrict__ V, const E* __restrict__ C,
-                 const int* __restrict__ patom, const void* __restrict__ pval, const int nslot, const int ncolE,
-                 const StepArgs<typename Elem<E>::S> A) {
+// Body of the column tile for block (bx, by, bz) = (x tile, y tile, column * nzc + z chunk).
+template <typename E, bool CPLX, int TX, int TY, int PF, int D, bool PREV, bool KB, bool VLOC, bool KIN>
+__device__ __forceinline__ void
+cheb_step_body(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __restrict__ Ynext,
+               const typename Elem<E>::S* __restrict__ V, const E* __restrict__ C,
+               const int* __restrict__ patom, const void* __restrict__ pval, const int nslot,
+               const StepArgs<typename Elem<E>::S> A, const int bx, const int by, const int bz) {
     using S = typename Elem<E>::S;
     using KV = typename std::conditional<CPLX, E, S>::type;   // KB value type at a grid point
     constexpr int R = FD_RADIUS;
@@ -231,9 +232,9 @@ cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __rest
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int col = blockIdx.z / A.nzc;
-    const int zc = blockIdx.z - col * A.nzc;
+    const int x0 = bx * TX, y0 = by * TY;
+    const int col = bz / A.nzc;
+    const int zc = bz - col * A.nzc;
     const int z0 = zc * A.zchunk;
     const int z1 = min(A.n3, z0 + A.zchunk);
     const int gx = x0 + tx, gy = y0 + ty;
@@ -377,6 +378,49 @@ cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __rest
         }
     }
     cp_async_wait<0>();
+}
+
+template <typename E, bool CPLX, int TX, int TY, int PF, int MINB, int D, bool PREV, bool KB, bool VLOC, bool KIN>
+__global__ void __launch_bounds__(TX * TY, MINB)
+cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __restrict__ Ynext,
+                 const typename Elem<E>::S* __restrict__ V, const E* __restrict__ C,
+                 const int* __restrict__ patom, const void* __restrict__ pval, const int nslot, const int ncolE,
+                 const StepArgs<typename Elem<E>::S> A) {
+    cheb_step_body<E, CPLX, TX, TY, PF, D, PREV, KB, VLOC, KIN>(Y, Yprev, Ynext, V, C, patom, pval, nslot, A,
+                                                                 blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---- several grids in one launch (independent cells of uneven size, FP32 real blocks) -----
+constexpr int MULTI_MAX = 64;
+}  // namespace
+struct MultiProblem {                 // one cell's block in a multi-grid launch of the column tile
+    StepArgs<float> A;                // grid, coefficients, recurrence step, z chunking
+    const float2* Y;
+    const float2* Yprev;
+    float2* Ynext;
+    const float* V;
+    const float2* C;
+    const int* patom;
+    const void* pval;
+    int nslot, tiles_x, tiles_y, cta_begin, cta_end;
+};
+namespace {
+__constant__ MultiProblem c_multi[MULTI_MAX];
+
+// grid: the CTAs of every problem, problem p owning [cta_begin, cta_end) (tiles_x * tiles_y * ncolE * nzc)
+template <int TX, int TY, int PF, int MINB, int D, bool PREV>
+__global__ void __launch_bounds__(TX * TY, MINB) cheb_multi_kernel(const int nprob) {
+    const int b = blockIdx.x;
+    int p = 0;
+    while (p + 1 < nprob && b >= c_multi[p].cta_end) ++p;
+    const MultiProblem& P = c_multi[p];
+    const int local = b - P.cta_begin;
+    const int bx = local % P.tiles_x;
+    const int rest = local / P.tiles_x;
+    const int by = rest % P.tiles_y;
+    const int bz = rest / P.tiles_y;
+    cheb_step_body<float2, false, TX, TY, PF, D, PREV, true, true, true>(P.Y, P.Yprev, P.Ynext, P.V, P.C, P.patom,
+                                                                          P.pval, P.nslot, P.A, bx, by, bz);
 }
 
 // ---- row-tile variant (FP32 blocks, n1 even) --------------------------------------------

@@ -1,0 +1,64 @@
+"""Several independent cells of uneven grid size filtered together: one column-tile stencil launch
+per Chebyshev step covers every cell.  Each cell's result must be bitwise the one of filtering it
+alone with the same tile, and the smallest cell is checked against the FP64 oracle."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import workloads  # noqa: E402
+from oracle import chefsi, ham, model  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_10431_gb300 import build
+    build.build()
+    import paper_2005_10431_gb300 as m
+    return m
+
+
+def test_multi_cell_filter_matches_single_cells_and_oracle(sd, monkeypatch):
+    monkeypatch.setenv("SDFT_STENCIL_VARIANT", "0")   # the column tile the multi-cell launch uses
+    cells = workloads.uneven_cells(count=6, seed=3)
+    ctxs, xs, ys, Vs, Xs = [], [], [], [], []
+    a, b, a0 = [], [], []
+    for i, c in enumerate(cells):
+        ctx = sd.sdft_create(c.L, c.n, c.pos, c.types, c.species, dict(nstates=c.nstates, precision=sd.SDFT_MIXED))
+        V = np.random.default_rng(i).normal(0, 0.3, c.ngrid)
+        sd.sdft_set_veff(ctx, 0, V)
+        X = workloads.initial_orbitals(50 + i, c.ngrid, c.nstates)
+        ctxs.append(ctx)
+        Vs.append(V)
+        Xs.append(X)
+        xs.append(sd.pack_block(X, sd.SDFT_MIXED))
+        ys.append(torch.empty_like(xs[-1]))
+        a.append(2.0 + 0.1 * i)
+        b.append(90.0 + i)
+        a0.append(-1.0 - 0.05 * i)
+    deg = 6
+    sd.sdft_chebyshev_filter_multi(ctxs, xs, ys, deg, a, b, a0)
+    for i, c in enumerate(cells):
+        y1 = torch.empty_like(xs[i])
+        sd.sdft_chebyshev_filter(ctxs[i], 0, 0, sd.SDFT_MIXED, xs[i], y1, c.nstates, deg, a[i], b[i], a0[i])
+        assert torch.equal(ys[i], y1), f"cell {i} ({c.n}) differs from its single-cell filter"
+    # the smallest cell against the FP64 oracle (FP32 filter tolerance 3e-5 per step)
+    i = int(np.argmin([c.ngrid for c in cells]))
+    c = cells[i]
+    P = model.projectors(c)
+    E = model.kb_energies(c)
+    ref = chefsi.chebyshev_filter(lambda Z: ham.apply_h(c, Z, Vs[i], P, E), Xs[i], deg, a[i], b[i], a0[i])
+    got = sd.unpack_block(ys[i], sd.SDFT_MIXED, False)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 3e-5 * deg
+
+
+def test_multi_cell_filter_rejects_complex_and_fp64(sd):
+    c = workloads.uneven_cells(count=1, seed=3)[0]
+    ctx = sd.sdft_create(c.L, c.n, c.pos, c.types, c.species, dict(nstates=c.nstates, precision=sd.SDFT_FP64))
+    x = torch.zeros((c.nstates, c.ngrid), dtype=torch.float64, device="cuda")
+    with pytest.raises(sd.SdftError):
+        sd.sdft_chebyshev_filter_multi([ctx], [x], [torch.empty_like(x)], 4, [2.0], [90.0], [-1.0])
