@@ -419,23 +419,53 @@ __global__ void fermi_kernel(const double* __restrict__ eig, const double* __res
         hi_s = emax + 50.0 * kT + 1.0;
     }
     __syncthreads();
+    // safeguarded Newton on N(mu) = N_e: the bracket [lo, hi] shrinks every step (bisection
+    // semantics as in the definition), the next trial point is the Newton step when it falls
+    // inside the bracket, else the midpoint
+    __shared__ double mu_s, red2[1024 / 32];
+    __shared__ int done_s;
+    if (threadIdx.x == 0) {
+        mu_s = 0.5 * (lo_s + hi_s);
+        done_s = 0;
+    }
+    __syncthreads();
     for (int it = 0; it < 200; ++it) {
-        const double lo = lo_s, hi = hi_s;
-        const double mid = 0.5 * (lo + hi);
-        double cnt = 0.0;
+        const double mid = mu_s;
+        double cnt = 0.0, der = 0.0;
         for (int i = threadIdx.x; i < total; i += blockDim.x) {
             const int k = (i / ns) % nk;
-            cnt += kw[k] * fs * 0.5 * (1.0 - tanh(0.5 * (eig[i] - mid) / kT));
+            const double f = 0.5 * (1.0 - tanh(0.5 * (eig[i] - mid) / kT));
+            cnt += kw[k] * fs * f;
+            der += kw[k] * fs * f * (1.0 - f) / kT;
         }
         cnt = block_reduce(cnt, 0);
+        {   // second sum through its own scratch row
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            for (int off = 16; off > 0; off >>= 1) der += __shfl_down_sync(0xffffffffu, der, off);
+            if (lane == 0) red2[warp] = der;
+            __syncthreads();
+            double r = red2[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r += red2[w];
+            der = r;
+        }
         if (threadIdx.x == 0) {
             if (cnt < nelec) lo_s = mid;
             else hi_s = mid;
+            double next = 0.5 * (lo_s + hi_s);
+            if (der > 0.0) {
+                const double newton = mid + (nelec - cnt) / der;
+                if (newton > lo_s && newton < hi_s) next = newton;
+            }
+            if (fabs(cnt - nelec) <= 1e-14 * fmax(1.0, nelec) || hi_s - lo_s < 1e-15 * fmax(1.0, fabs(mid))) {
+                done_s = 1;
+                next = mid;
+            }
+            mu_s = next;
         }
         __syncthreads();
-        if (hi_s - lo_s < 1e-15 * fmax(1.0, fabs(mid))) break;
+        if (done_s) break;
     }
-    const double mu = 0.5 * (lo_s + hi_s);
+    const double mu = mu_s;
     double ts = 0.0, eb = 0.0;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
         const int k = (i / ns) % nk;
@@ -1252,8 +1282,8 @@ void fermi_device(sdft_ctx* c, const double* eig, double* occ, double* out) {
     double* kw = c->scal + 256;
     SDFT_CUDA(cudaMemcpyAsync(kw, c->kw.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, c->stream));
     const double fs = c->opt.nspin == 1 ? 2.0 : 1.0;
-    fermi_kernel<<<1, 1024, 0, c->stream>>>(eig, kw, c->opt.nspin, nk, c->opt.nstates, c->nelec, c->opt.kT, fs, occ,
-                                            out);
+    fermi_kernel<<<1, 256, 0, c->stream>>>(eig, kw, c->opt.nspin, nk, c->opt.nstates, c->nelec, c->opt.kT, fs, occ,
+                                           out);
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);
 }
