@@ -120,32 +120,61 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// Load the [128 rows x 64 points] FP32 tile (rows = orbitals row0.., paired layout) starting at
-// grid point g0, split into bf16 hi/lo and store into the two swizzled tiles.  Rows >= ncol and
-// points >= g1 are zero.  Each work item = one orbital pair x 8 consecutive points (16-byte chunk
-// per row and part).
-__device__ __forceinline__ void stage_tile(const float* __restrict__ Y, long long ng, int ncol, int row0,
-                                           long long g0, long long g1, unsigned char* hi_tile,
-                                           unsigned char* lo_tile) {
-    for (int item = threadIdx.x; item < (TC_M / 2) * (TC_K / 8); item += blockDim.x) {
-        const int pr = item / (TC_K / 8);          // pair within the tile
-        const int ch = item - pr * (TC_K / 8);     // 8-point chunk
-        const int r0 = 2 * pr;                     // rows r0, r0+1 = orbitals row0+r0, +1
-        const int orb = row0 + r0;
-        __align__(16) __nv_bfloat16 h0[8], l0[8], h1[8], l1[8];
+// Gram operand tiles [128 orbitals x 64 points] of the paired FP32 layout: the global loads of a
+// tile's items go to registers first (all tiles of a stage are requested before any is converted,
+// and the next stage is requested while the current one's MMAs run), then the values are split
+// into bf16 hi/lo and stored.  Items: 2 per thread (256 threads, 64 orbital pairs x 8 chunks).
+constexpr int TC_ITEMS = (TC_M / 2) * (TC_K / 8) / 256;
+
+struct TileRegs {
+    float4 v[TC_ITEMS][4];   // 8 float2 (orbital pair, 8 consecutive points) per item
+};
+
+__device__ __forceinline__ void load_tile(const float* __restrict__ Y, long long ng, int ncol, int row0,
+                                          long long g0, long long g1, TileRegs& R) {
+#pragma unroll
+    for (int it = 0; it < TC_ITEMS; ++it) {
+        const int item = threadIdx.x + it * 256;
+        const int pr = item / (TC_K / 8);
+        const int ch = item - pr * (TC_K / 8);
+        const int orb = row0 + 2 * pr;
         const long long gs = g0 + ch * 8;
-        if (orb < ncol) {
-            const float2* src = reinterpret_cast<const float2*>(Y) + ((long long)(orb >> 1) * ng + gs);
+        const float2* src = reinterpret_cast<const float2*>(Y) + ((long long)(orb >> 1) * ng + gs);
+        // 16-byte loads need an even ngrid (gs is a multiple of 8, the column offset (orb/2) ngrid)
+        const bool vec = (ng & 1) == 0;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                float2 v = make_float2(0.f, 0.f);
-                if (gs + e < g1) v = __ldg(src + e);
-                split_bf16(v.x, h0[e], l0[e]);
-                split_bf16(v.y, h1[e], l1[e]);
+        for (int q = 0; q < 4; ++q) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (orb < ncol) {
+                if (vec && gs + 2 * q + 1 < g1) {
+                    v = __ldg(reinterpret_cast<const float4*>(src + 2 * q));
+                } else {
+                    float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+                    if (gs + 2 * q < g1) w0 = __ldg(src + 2 * q);
+                    if (gs + 2 * q + 1 < g1) w1 = __ldg(src + 2 * q + 1);
+                    v = make_float4(w0.x, w0.y, w1.x, w1.y);
+                }
             }
-        } else {
+            R.v[it][q] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ void store_tile(const TileRegs& R, unsigned char* hi_tile, unsigned char* lo_tile) {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) h0[e] = l0[e] = h1[e] = l1[e] = __float2bfloat16_rn(0.f);
+    for (int it = 0; it < TC_ITEMS; ++it) {
+        const int item = threadIdx.x + it * 256;
+        const int pr = item / (TC_K / 8);
+        const int ch = item - pr * (TC_K / 8);
+        const int r0 = 2 * pr;
+        __align__(16) __nv_bfloat16 h0[8], l0[8], h1[8], l1[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = R.v[it][q];
+            split_bf16(v.x, h0[2 * q], l0[2 * q]);
+            split_bf16(v.y, h1[2 * q], l1[2 * q]);
+            split_bf16(v.z, h0[2 * q + 1], l0[2 * q + 1]);
+            split_bf16(v.w, h1[2 * q + 1], l1[2 * q + 1]);
         }
         *reinterpret_cast<uint4*>(hi_tile + sw128_off(r0, ch * 8)) = *reinterpret_cast<uint4*>(h0);
         *reinterpret_cast<uint4*>(lo_tile + sw128_off(r0, ch * 8)) = *reinterpret_cast<uint4*>(l0);
@@ -186,6 +215,14 @@ gram_tc_kernel(const float* __restrict__ Y, const float* __restrict__ HY, int nc
     constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
     bool ok = true;
 
+    TileRegs ra, rb, rc;   // the next stage's operands, requested one stage ahead
+    auto load_stage = [&](int t) {
+        const long long gt = g0 + (long long)t * TC_K;
+        load_tile(Y, ng, ncol, row_i, gt, g1, ra);
+        if (!diag) load_tile(Y, ng, ncol, row_j, gt, g1, rb);
+        load_tile(HY, ng, ncol, row_j, gt, g1, rc);
+    };
+    if (ntile > 0) load_stage(0);
     for (int t = 0; t < ntile; ++t) {
         const int s = t % NSTAGE;
         unsigned char* st = smem + s * STAGE_BYTES;
@@ -198,10 +235,9 @@ gram_tc_kernel(const float* __restrict__ Y, const float* __restrict__ HY, int nc
                 break;
             }
         }
-        const long long gt = g0 + (long long)t * TC_K;
-        stage_tile(Y, ng, ncol, row_i, gt, g1, a_hi, a_lo);
-        if (!diag) stage_tile(Y, ng, ncol, row_j, gt, g1, b_hi, b_lo);
-        stage_tile(HY, ng, ncol, row_j, gt, g1, c_hi, c_lo);
+        store_tile(ra, a_hi, a_lo);
+        if (!diag) store_tile(rb, b_hi, b_lo);
+        store_tile(rc, c_hi, c_lo);
         fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -224,6 +260,7 @@ gram_tc_kernel(const float* __restrict__ Y, const float* __restrict__ HY, int nc
             }
             mma_commit(&bars[s]);
         }
+        if (t + 1 < ntile) load_stage(t + 1);   // in flight while this stage's MMAs run
     }
     // drain: wait for the last commit of every stage that was used
     if (ok) {
@@ -302,49 +339,9 @@ __global__ void gram_tc_reduce_kernel(const float* __restrict__ part, int nsplit
 // ---------------------------------------------------------------------------------------
 constexpr int ROT_STAGE_BYTES = 4 * TILE_BYTES;   // A hi/lo, B hi/lo
 
-// A tile: rows = grid points g0.. (128), k = orbitals k0..k0+63 of the paired layout.
-// Work item = one grid point x 16 consecutive orbitals (two 16-byte chunks per part).
-__device__ __forceinline__ void stage_rot_a(const float* __restrict__ Y, long long ng, int ncol, long long g0,
-                                            int k0, unsigned char* hi_tile, unsigned char* lo_tile) {
-    for (int item = threadIdx.x; item < TC_M * (TC_K / 16); item += blockDim.x) {
-        const int r = item % TC_M;           // consecutive threads: consecutive grid points
-        const int q = item / TC_M;           // 16-orbital group
-        const long long g = g0 + r;
-        __align__(16) __nv_bfloat16 h[16], l[16];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int k = k0 + 16 * q + 2 * e;          // orbital pair (k, k+1)
-            float2 v = make_float2(0.f, 0.f);
-            if (g < ng && k < ncol) v = __ldg(reinterpret_cast<const float2*>(Y) + ((long long)(k >> 1) * ng + g));
-            split_bf16(v.x, h[2 * e], l[2 * e]);
-            split_bf16(v.y, h[2 * e + 1], l[2 * e + 1]);
-        }
-        *reinterpret_cast<uint4*>(hi_tile + sw128_off(r, 16 * q)) = *reinterpret_cast<uint4*>(h);
-        *reinterpret_cast<uint4*>(hi_tile + sw128_off(r, 16 * q + 8)) = *reinterpret_cast<uint4*>(h + 8);
-        *reinterpret_cast<uint4*>(lo_tile + sw128_off(r, 16 * q)) = *reinterpret_cast<uint4*>(l);
-        *reinterpret_cast<uint4*>(lo_tile + sw128_off(r, 16 * q + 8)) = *reinterpret_cast<uint4*>(l + 8);
-    }
-}
-
-// B tile: rows = output orbitals j0.. (128), k = input orbitals k0..k0+63: B[j][k] = Q[k + j n]
-__device__ __forceinline__ void stage_rot_b(const float* __restrict__ Q32, int ncol, int j0, int k0,
-                                            unsigned char* hi_tile, unsigned char* lo_tile) {
-    for (int item = threadIdx.x; item < TC_N * (TC_K / 8); item += blockDim.x) {
-        const int r = item / (TC_K / 8);
-        const int ch = item - r * (TC_K / 8);
-        const int j = j0 + r;
-        __align__(16) __nv_bfloat16 h[8], l[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int k = k0 + ch * 8 + e;
-            const float v = (j < ncol && k < ncol) ? Q32[(long long)k + (long long)j * ncol] : 0.f;
-            split_bf16(v, h[e], l[e]);
-        }
-        *reinterpret_cast<uint4*>(hi_tile + sw128_off(r, ch * 8)) = *reinterpret_cast<uint4*>(h);
-        *reinterpret_cast<uint4*>(lo_tile + sw128_off(r, ch * 8)) = *reinterpret_cast<uint4*>(l);
-    }
-}
-
+// A tile: rows = grid points g0.. (128), k = orbitals k0..k0+63 of the paired layout (a work item
+// = one grid point x 16 consecutive orbitals); B tile: rows = output orbitals j0.. (128),
+// k = input orbitals: B[j][k] = Q[k + j n].  Both are staged inside the kernel's main loop.
 __global__ void __launch_bounds__(256, 1)
 rotate_tc_kernel(const float* __restrict__ Y, const float* __restrict__ Q32, float* __restrict__ X, int ncol,
                  long long ng, int* __restrict__ err) {
@@ -367,6 +364,38 @@ rotate_tc_kernel(const float* __restrict__ Y, const float* __restrict__ Q32, flo
     const uint32_t tmem = *tmem_slot;
     constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
     bool ok = true;
+    // operands of the next stage, requested one stage ahead (in flight while the MMAs run)
+    constexpr int NA = TC_M * (TC_K / 16) / 256, NB = TC_N * (TC_K / 8) / 256;
+    float2 va[NA][8];
+    float vb[NB][8];
+    auto load_stage = [&](int t) {
+        const int k0 = t * TC_K;
+#pragma unroll
+        for (int it = 0; it < NA; ++it) {
+            const int item = threadIdx.x + it * 256;
+            const int r = item % TC_M, q = item / TC_M;
+            const long long g = g0 + r;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = k0 + 16 * q + 2 * e;
+                va[it][e] = (g < ng && k < ncol)
+                                ? __ldg(reinterpret_cast<const float2*>(Y) + ((long long)(k >> 1) * ng + g))
+                                : make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < NB; ++it) {
+            const int item = threadIdx.x + it * 256;
+            const int r = item / (TC_K / 8), ch = item - r * (TC_K / 8);
+            const int j = j0 + r;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int k = k0 + ch * 8 + e;
+                vb[it][e] = (j < ncol && k < ncol) ? __ldg(Q32 + (long long)k + (long long)j * ncol) : 0.f;
+            }
+        }
+    };
+    if (nk > 0) load_stage(0);
     for (int t = 0; t < nk; ++t) {
         const int s = t % NSTAGE;
         unsigned char* st = smem + s * ROT_STAGE_BYTES;
@@ -377,8 +406,33 @@ rotate_tc_kernel(const float* __restrict__ Y, const float* __restrict__ Q32, flo
                 break;
             }
         }
-        stage_rot_a(Y, ng, ncol, g0, t * TC_K, a_hi, a_lo);
-        stage_rot_b(Q32, ncol, j0, t * TC_K, b_hi, b_lo);
+        {
+#pragma unroll
+            for (int it = 0; it < NA; ++it) {
+                const int item = threadIdx.x + it * 256;
+                const int r = item % TC_M, q = item / TC_M;
+                __align__(16) __nv_bfloat16 h[16], l[16];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    split_bf16(va[it][e].x, h[2 * e], l[2 * e]);
+                    split_bf16(va[it][e].y, h[2 * e + 1], l[2 * e + 1]);
+                }
+                *reinterpret_cast<uint4*>(a_hi + sw128_off(r, 16 * q)) = *reinterpret_cast<uint4*>(h);
+                *reinterpret_cast<uint4*>(a_hi + sw128_off(r, 16 * q + 8)) = *reinterpret_cast<uint4*>(h + 8);
+                *reinterpret_cast<uint4*>(a_lo + sw128_off(r, 16 * q)) = *reinterpret_cast<uint4*>(l);
+                *reinterpret_cast<uint4*>(a_lo + sw128_off(r, 16 * q + 8)) = *reinterpret_cast<uint4*>(l + 8);
+            }
+#pragma unroll
+            for (int it = 0; it < NB; ++it) {
+                const int item = threadIdx.x + it * 256;
+                const int r = item / (TC_K / 8), ch = item - r * (TC_K / 8);
+                __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) split_bf16(vb[it][e], h[e], l[e]);
+                *reinterpret_cast<uint4*>(b_hi + sw128_off(r, ch * 8)) = *reinterpret_cast<uint4*>(h);
+                *reinterpret_cast<uint4*>(b_lo + sw128_off(r, ch * 8)) = *reinterpret_cast<uint4*>(l);
+            }
+        }
         fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -393,6 +447,7 @@ rotate_tc_kernel(const float* __restrict__ Y, const float* __restrict__ Q32, flo
             }
             mma_commit(&bars[s]);
         }
+        if (t + 1 < nk) load_stage(t + 1);
     }
     if (ok) {
         for (int t = std::max(0, nk - NSTAGE); t < nk; ++t) {

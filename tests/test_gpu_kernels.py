@@ -197,7 +197,7 @@ def test_subspace_matrices_and_rotation_mixed(sd):
     assert _relerr(sd.unpack_block(x, 1, False), ref) < 1e-5
 
 
-@pytest.mark.parametrize("n", [(9, 10, 11), (40, 40, 40)])
+@pytest.mark.parametrize("n", [(9, 10, 11), (9, 11, 13), (40, 40, 40)])
 def test_gram_tcgen05_bf16x3_matches_fp64(sd, n):
     # 154 orbitals (two 128-row tiles, three tile pairs): the tensor-core BF16x3 path.  The split
     # product drops lo*lo and the bf16 remainders: ~2^-16 relative per product, far less after
@@ -222,7 +222,7 @@ def test_gram_tcgen05_bf16x3_matches_fp64(sd, n):
     assert np.max(np.abs(h.cpu().numpy().T - H_ref) / scale) < 2e-5
 
 
-@pytest.mark.parametrize("n", [(9, 10, 11), (40, 40, 40)])
+@pytest.mark.parametrize("n", [(9, 10, 11), (9, 11, 13), (40, 40, 40)])
 def test_rotation_tcgen05_bf16x3_matches_fp64(sd, n):
     # X = Y Q with 154 orbitals on the tensor cores (two 128-column tiles, three K tiles, a
     # ragged last grid tile): BF16x3 of FP32 operands, error ~2^-16 of |Y||Q| per term.
