@@ -216,7 +216,7 @@ __device__ __forceinline__ void
 cheb_step_body(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __restrict__ Ynext,
                const typename Elem<E>::S* __restrict__ V, const E* __restrict__ C,
                const int* __restrict__ patom, const void* __restrict__ pval, const int nslot,
-               const StepArgs<typename Elem<E>::S> A, const int bx, const int by, const int bz) {
+               const StepArgs<typename Elem<E>::S>& A, const int bx, const int by, const int bz) {
     using S = typename Elem<E>::S;
     using KV = typename std::conditional<CPLX, E, S>::type;   // KB value type at a grid point
     constexpr int R = FD_RADIUS;
@@ -385,7 +385,8 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __restrict__ Ynext,
                  const typename Elem<E>::S* __restrict__ V, const E* __restrict__ C,
                  const int* __restrict__ patom, const void* __restrict__ pval, const int nslot, const int ncolE,
-                 const StepArgs<typename Elem<E>::S> A) {
+                 const __grid_constant__ StepArgs<typename Elem<E>::S> A) {
+    // A is referenced in place (grid constant): no copy of the argument block
     cheb_step_body<E, CPLX, TX, TY, PF, D, PREV, KB, VLOC, KIN>(Y, Yprev, Ynext, V, C, patom, pval, nslot, A,
                                                                  blockIdx.x, blockIdx.y, blockIdx.z);
 }
