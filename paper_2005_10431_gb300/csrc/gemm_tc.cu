@@ -197,7 +197,6 @@ gram_tc_kernel(const float* __restrict__ Y, const float* __restrict__ HY, int nc
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NSTAGE);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const TilePair tp = pairs[blockIdx.x];
-    const bool diag = tp.ti == tp.tj;
     const int row_i = tp.ti * TC_M, row_j = tp.tj * TC_N;
     const long long g0 = blockIdx.y * chunk;
     const long long g1 = min(ng, g0 + chunk);
@@ -212,22 +211,24 @@ gram_tc_kernel(const float* __restrict__ Y, const float* __restrict__ HY, int nc
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+    // one MMA computes both accumulators: A (Y_i) against the stacked 256-row operand [Y_j; HY_j]
+    constexpr uint32_t idesc = idesc_bf16(TC_M, 2 * TC_N);
     bool ok = true;
 
     TileRegs ra, rb, rc;   // the next stage's operands, requested one stage ahead
     auto load_stage = [&](int t) {
         const long long gt = g0 + (long long)t * TC_K;
         load_tile(Y, ng, ncol, row_i, gt, g1, ra);
-        if (!diag) load_tile(Y, ng, ncol, row_j, gt, g1, rb);
+        load_tile(Y, ng, ncol, row_j, gt, g1, rb);
         load_tile(HY, ng, ncol, row_j, gt, g1, rc);
     };
     if (ntile > 0) load_stage(0);
     for (int t = 0; t < ntile; ++t) {
         const int s = t % NSTAGE;
         unsigned char* st = smem + s * STAGE_BYTES;
-        unsigned char *a_hi = st, *a_lo = st + TILE_BYTES, *b_hi = st + 2 * TILE_BYTES, *b_lo = st + 3 * TILE_BYTES;
-        unsigned char *c_hi = st + 4 * TILE_BYTES, *c_lo = st + 5 * TILE_BYTES;
+        // stage: A hi, A lo, then [B hi; C hi] and [B lo; C lo] as 256-row K-major operands
+        unsigned char *a_hi = st, *a_lo = st + TILE_BYTES, *b_hi = st + 2 * TILE_BYTES, *c_hi = st + 3 * TILE_BYTES;
+        unsigned char *b_lo = st + 4 * TILE_BYTES, *c_lo = st + 5 * TILE_BYTES;
         // the MMAs that read this stage two tiles ago must be complete before it is refilled
         if (t >= NSTAGE) {
             if (!mbar_wait(&bars[s], (uint32_t)(((t - NSTAGE) / NSTAGE) & 1))) {
@@ -236,27 +237,22 @@ gram_tc_kernel(const float* __restrict__ Y, const float* __restrict__ HY, int nc
             }
         }
         store_tile(ra, a_hi, a_lo);
-        if (!diag) store_tile(rb, b_hi, b_lo);
+        store_tile(rb, b_hi, b_lo);
         store_tile(rc, c_hi, c_lo);
         fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
             fence_after_sync();
             const uint32_t ah = su32(a_hi), al = su32(a_lo);
-            const uint32_t bh = diag ? ah : su32(b_hi), bl = diag ? al : su32(b_lo);
-            const uint32_t ch = su32(c_hi), cl = su32(c_lo);
+            const uint32_t bch = su32(b_hi), bcl = su32(b_lo);   // [B; C] hi and lo, 256 rows each
 #pragma unroll
             for (int kk = 0; kk < TC_K / 16; ++kk) {
                 const uint32_t ko = kk * 32;  // 16 bf16 = 32 bytes along the swizzled row
                 const uint32_t acc0 = (t > 0 || kk > 0) ? 1u : 0u;
-                // M += Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T
-                mma_bf16(tmem, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, acc0);
-                mma_bf16(tmem, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
-                mma_bf16(tmem, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
-                // Hs += Ahi Chi^T + Ahi Clo^T + Alo Chi^T
-                mma_bf16(tmem + 128, sw128_desc(ah + ko), sw128_desc(ch + ko), idesc, acc0);
-                mma_bf16(tmem + 128, sw128_desc(ah + ko), sw128_desc(cl + ko), idesc, 1u);
-                mma_bf16(tmem + 128, sw128_desc(al + ko), sw128_desc(ch + ko), idesc, 1u);
+                // [M | Hs] += Ahi [B;C]hi^T + Ahi [B;C]lo^T + Alo [B;C]hi^T   (TMEM columns 0..255)
+                mma_bf16(tmem, sw128_desc(ah + ko), sw128_desc(bch + ko), idesc, acc0);
+                mma_bf16(tmem, sw128_desc(ah + ko), sw128_desc(bcl + ko), idesc, 1u);
+                mma_bf16(tmem, sw128_desc(al + ko), sw128_desc(bch + ko), idesc, 1u);
             }
             mma_commit(&bars[s]);
         }
