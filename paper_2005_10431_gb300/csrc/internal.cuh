@@ -100,6 +100,9 @@ struct KBProblem {
     const void* val;
     const double* gamma;
     int cap;
+    int natom;      // atoms (rows of C per column)
+    int ncolE;      // block columns (paired columns in the real FP32 layout)
+    long long ng;   // grid points per column
 };
 
 struct Problem {              // one (spin, k) eigenproblem
@@ -214,6 +217,8 @@ struct sdft_ctx {
     // pinned copies of the step tables (sources of the graph's upload) and the captured filter
     sdft::RowProblem* g_rtab_pin = nullptr;
     sdft::KBProblem* g_ktab_pin = nullptr;
+    sdft::KBProblem* m_ktab = nullptr;   // multi-cell filter: KB tables of every (step, cell)
+    int m_ktab_cap = 0;
     int g_pin_cap = 0;
     cudaGraphExec_t g_graph = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
@@ -331,6 +336,7 @@ int group_variant_f32(sdft_ctx* c, bool cplx, int ncolE);
 void launch_group_step_f32(sdft_ctx* c, bool cplx, int variant, const RowProblem* grp, int nprob, int ncolE,
                            bool prev, bool haskb);
 void launch_group_project_f32(sdft_ctx* c, bool cplx, const KBProblem* grp, int nprob, int ncolE);
+void launch_multi_project_f32(sdft_ctx* c, const KBProblem* grp, int nprob, int max_natom, int max_ncolE);
 int autotune_group_f32(sdft_ctx* c, bool cplx, const RowProblem* grp, int nprob, int ncolE, bool haskb);
 // Chebyshev filter of the FP32 real blocks of several cells (contexts with their own grids) with
 // one column-tile stencil launch per step (scf.cu; kernels in stencil_f32.cu)

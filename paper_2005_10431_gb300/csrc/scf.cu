@@ -371,7 +371,7 @@ static void chefsi_pass_group(sdft_ctx* c, const std::vector<Problem*>& G, int v
             base.phr[d] = (float)cos(2.0 * M_PI * kd);
             base.phi[d] = (float)sin(2.0 * M_PI * kd);
         }
-        KBProblem kbase{nullptr, Cp, kb.cnt, kb.idx, kb.val32, kb.gamma, kb.cap};
+        KBProblem kbase{nullptr, Cp, kb.cnt, kb.idx, kb.val32, kb.gamma, kb.cap, kb.natom, ncolE, ng};
         const double e = 0.5 * (b - a), cc = 0.5 * (b + a);
         const double sigma1 = e / (a0 - cc);
         double sigma = sigma1;

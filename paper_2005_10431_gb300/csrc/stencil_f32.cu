@@ -201,15 +201,45 @@ void chebyshev_filter_multi(const std::vector<sdft_ctx*>& ctxs, const std::vecto
         ctas += (long long)((c->n[0] + 31) / 32) * ((c->n[1] + 7) / 8) * (c->opt.nstates / 2) * nzc[i];
     }
     auto slot = [&](int i, int k) -> float2* { return ring[i][(((2 - (m - k)) % 3) + 3) % 3]; };
+    // KB projections of every (step, cell): one table, uploaded once, one grouped launch per step
+    sdft_ctx* c0 = ctxs[0];
+    std::vector<KBProblem> ktab;
+    std::vector<int> kcell;
+    int max_natom = 0, max_ncolE = 0;
+    for (int i = 0; i < n; ++i) {
+        const KBTables& kb = ctxs[i]->kb[0];
+        if (kb.S == 0 || kb.natom == 0) continue;
+        kcell.push_back(i);
+        max_natom = std::max(max_natom, kb.natom);
+        max_ncolE = std::max(max_ncolE, ctxs[i]->opt.nstates / 2);
+    }
+    const int nk = (int)kcell.size();
+    if (nk > 0) {
+        ktab.reserve((size_t)m * nk);
+        for (int k = 1; k <= m; ++k)
+            for (int i : kcell) {
+                sdft_ctx* c = ctxs[i];
+                const KBTables& kb = c->kb[0];
+                const float2* cur = k == 1 ? (const float2*)X[i] : slot(i, k - 1);
+                ktab.push_back(KBProblem{cur, c->C32, kb.cnt, kb.idx, kb.val32, kb.gamma, kb.cap, kb.natom,
+                                         c->opt.nstates / 2, c->ng});
+            }
+        if (c0->m_ktab_cap < (int)ktab.size()) {
+            c0->m_ktab = (KBProblem*)ctx_alloc(c0, sizeof(KBProblem) * ktab.size());
+            c0->m_ktab_cap = (int)ktab.size();
+        }
+        // pageable source: the copy is staged before the call returns, so ktab may go out of scope
+        SDFT_CUDA(cudaMemcpyAsync(c0->m_ktab, ktab.data(), sizeof(KBProblem) * ktab.size(), cudaMemcpyHostToDevice,
+                                  c0->stream));
+    }
     std::vector<MultiProblem> probs(n);
     for (int k = 1; k <= m; ++k) {
+        if (nk > 0) launch_multi_project_f32(c0, c0->m_ktab + (size_t)(k - 1) * nk, nk, max_natom, max_ncolE);
         for (int i = 0; i < n; ++i) {
             sdft_ctx* c = ctxs[i];
-            const int ncolE = c->opt.nstates / 2;
             const float2* cur = k == 1 ? (const float2*)X[i] : slot(i, k - 1);
             const float2* prv = k == 1 ? nullptr : (k == 2 ? (const float2*)X[i] : slot(i, k - 2));
             const bool kb = c->kb[0].S > 0;
-            if (kb) launch_kb_project<float2>(c, 0, cur, (float2*)c->C32, ncolE);
             double alpha, beta = 0.0;
             if (k == 1) {
                 alpha = sigma1[i] / e[i];
@@ -236,6 +266,10 @@ void chebyshev_filter_multi(const std::vector<sdft_ctx*>& ctxs, const std::vecto
 
 void launch_group_project_f32(sdft_ctx* c, bool cplx, const KBProblem* grp, int nprob, int ncolE) {
     launch_project_group_impl<float2>(c, grp, nprob, ncolE, cplx);
+}
+
+void launch_multi_project_f32(sdft_ctx* c, const KBProblem* grp, int nprob, int max_natom, int max_ncolE) {
+    launch_project_multi_impl<float2>(c, grp, nprob, max_natom, max_ncolE);
 }
 
 }  // namespace sdft

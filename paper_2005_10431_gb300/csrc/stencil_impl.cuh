@@ -731,9 +731,13 @@ kb_project_kernel(const E* __restrict__ Y_, E* __restrict__ C_, const int* __res
         val = P.val;
         gamma = P.gamma;
         cap = P.cap;
+        natom = P.natom;
+        ncolE = P.ncolE;
+        ng = P.ng;
     }
     const int a = blockIdx.x;
     const int c0 = blockIdx.y * NC;
+    if (a >= natom || c0 >= ncolE) return;   // grouped launch sized for the largest problem
     const int m = cnt[a];
     E acc[NC];
 #pragma unroll
@@ -1004,6 +1008,20 @@ void launch_project_group_impl(sdft_ctx* c, const KBProblem* grp, int nprob, int
         kb_project_kernel<E, false, NC><<<grid, 256, 0, c->stream>>>(nullptr, nullptr, nullptr, nullptr, nullptr,
                                                                     nullptr, 0, natom, ncolE, c->ng, grp);
     }
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+// one launch over problems of different sizes (cells of a multi-cell filter): grid sized for the
+// largest, blocks past a problem's atoms or columns return at once
+template <typename E>
+void launch_project_multi_impl(sdft_ctx* c, const KBProblem* grp, int nprob, int max_natom, int max_ncolE) {
+    if (max_natom == 0 || max_ncolE == 0 || nprob == 0) return;
+    constexpr int NC = 4;
+    dim3 grid(max_natom, (max_ncolE + NC - 1) / NC, nprob);
+    ScopedTimer timer(c, SDFT_K_KB_PROJECT);
+    kb_project_kernel<E, false, NC><<<grid, 256, 0, c->stream>>>(nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                0, 0, 0, 0, grp);
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);
 }
