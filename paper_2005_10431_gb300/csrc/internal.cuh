@@ -139,7 +139,12 @@ struct sdft_ctx {
     std::vector<void*> owned;
     cusolverDnHandle_t solver = nullptr;
     syevjInfo_t syevj_params = nullptr;
-    int eig_method = -1;          // -1: batched Jacobi for n <= 64 else sygvd/hegvd; 0: sygvd/hegvd; 1: sygvj (real)
+    int eig_method = -1;          // -1: batched Jacobi for n <= 64, FP32 + FP64 refinement for real mixed-precision
+                                  //     n <= 160, else sygvd/hegvd; 0: sygvd/hegvd; 1: sygvj (real);
+                                  //  2: FP32 + refinement wherever it applies, without fallback
+    double* reig_buf = nullptr;   // scratch of the refined eigensolver (allocated on first use)
+    int reig_last_status = 0;     // its last status word (0 = accepted)
+    int reig_fallbacks = 0;       // refined solves rejected and redone by cuSOLVER
     // device pointer tables of batched launches (grown on demand) and their host staging copy
     void** ptab_dev = nullptr;
     int* pinfo_dev = nullptr;
@@ -312,6 +317,8 @@ void subspace_gram_noalloc(int precision, bool cplx, const void* Y, const void* 
                            double* M, double* Hs, cudaStream_t stream);
 // solve Hs q = lambda M q (FP64); Q overwrites Hs; eig ascending; throws CHOLESKY on failure
 void generalized_eig(sdft_ctx* c, bool cplx, double* M, double* Hs, double* eig, int ncol);
+bool refined_eig_supported(int n);
+bool refined_generalized_eig(sdft_ctx* c, const double* M, const double* Hs, double* Q, double* eig, int n);
 // X = Y Q (Q FP64 column-major)
 void rotate_block(sdft_ctx* c, int precision, bool cplx, const void* Y, const double* Q, void* X,
                   int ncol);
