@@ -249,7 +249,11 @@ sdft_status sdft_subspace_matrices_noalloc(int precision, int is_complex, const 
  * column-major ncol x ncol device matrices (double2 for is_complex).  M must be positive definite.
  * On return Hs holds Q (Q^H M Q = I, eigenvector j in column j), eig (device, ncol) ascending; M is
  * overwritten (scratch).  ncol <= 64 uses the library's one-CTA Cholesky + Jacobi solver (unless
- * SDFT_EIGEN=0 selects cuSOLVER), larger ncol cuSOLVER sygvd/hegvd, both after diagonal
+ * SDFT_EIGEN=0 selects cuSOLVER); a real problem with 64 < ncol <= 160 on an SDFT_MIXED context
+ * uses an FP32 solve refined to FP64 accuracy (Ogita-Aishima steps + Rayleigh-Ritz inside
+ * clusters of near-degenerate eigenvalues), accepted only if its FP64 residual and M-orthonormality
+ * defect are below 1e-10 relative, else redone by cuSOLVER (SDFT_EIGEN=2 forces it on any context
+ * and reports a rejection as an error instead); otherwise cuSOLVER sygvd/hegvd.  All after diagonal
  * equilibration.  SDFT_ERR_CHOLESKY if M is not positive definite. */
 sdft_status sdft_subspace_eig(sdft_ctx* ctx, int is_complex, double* m, double* hs, double* eig, int ncol);
 
