@@ -162,6 +162,18 @@ const char* sdft_last_error(const sdft_ctx* ctx);
  * current orbitals (seeded, or given by sdft_set_orbitals).  Returns NOT_CONVERGED with the
  * partial result filled in if max_scf is reached, CHOLESKY if the overlap matrix breaks down. */
 sdft_status sdft_scf(sdft_ctx* ctx, sdft_result* out);
+
+/* The SCFs of n distinct contexts in lockstep (paper Sec. 2.1's SCF, batched over independent
+ * cells; the paper runs such problems in separate groups of processes).  Per iteration every
+ * running context computes its potential, then the CheFSI passes: cells in mixed precision with
+ * one real Gamma-point problem, sharing one stream, with equal degree and pass count are filtered
+ * together (sdft_chebyshev_filter_multi: one KB projection and one stencil launch per Chebyshev
+ * step for all of them, column-tile stencil), each followed by its own Rayleigh-Ritz; other
+ * contexts run their passes alone.  A context stops at its own convergence or max_scf.
+ * out: host array of n results, filled for every context.  Returns the first non-OK status in
+ * context order (NOT_CONVERGED if a context did not converge); an error inside any context
+ * aborts the batch and is reported on ctxs[0] (and copied to the others' sdft_last_error). */
+sdft_status sdft_batch_scf(sdft_ctx* const* ctxs, int n, sdft_result* out);
 /* Re-seed the initial orbitals of every problem from opt.seed (as at create) and reset the
  * density guess to the SAD (or last user) density, so that sdft_scf can be repeated. */
 sdft_status sdft_reset(sdft_ctx* ctx);

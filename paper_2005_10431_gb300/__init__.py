@@ -17,7 +17,7 @@ from ._lib import (SDFT_FP64, SDFT_MIXED, SDFT_GUESS_SAD, SDFT_GUESS_USER, sdft_
 
 __all__ = [
     "SdftError", "Context", "SDFT_FP64", "SDFT_MIXED", "sdft_default_options", "sdft_create", "sdft_destroy",
-    "sdft_scf", "sdft_reset", "sdft_get_eigenvalues", "sdft_get_occupations", "sdft_get_density",
+    "sdft_scf", "sdft_batch_scf", "sdft_reset", "sdft_get_eigenvalues", "sdft_get_occupations", "sdft_get_density",
     "sdft_set_density", "sdft_get_forces", "sdft_get_scf_log", "sdft_get_pseudocharge", "sdft_get_sad_density",
     "sdft_set_orbitals", "sdft_get_orbitals", "sdft_set_veff", "sdft_apply_h", "sdft_chebyshev_filter",
     "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_subspace_matrices_noalloc", "sdft_subspace_eig", "sdft_chebyshev_filter_multi", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
@@ -152,6 +152,23 @@ def sdft_scf(ctx: Context, raise_not_converged: bool = False) -> dict:
         _check(code, ctx.handle)
     out = {name: getattr(r, name) for name, _ in sdft_result._fields_}
     out["status"] = code
+    return out
+
+
+def sdft_batch_scf(ctxs, raise_not_converged: bool = False) -> list:
+    """The SCFs of several contexts in lockstep (cells that qualify share the multi-cell filter);
+    one result dict per context, as sdft_scf returns."""
+    n = len(ctxs)
+    handles = (C.c_void_p * n)(*[c.handle for c in ctxs])
+    res = (sdft_result * n)()
+    code = _lib.lib().sdft_batch_scf(handles, n, res)
+    if code != _lib.SDFT_ERR_NOT_CONVERGED or raise_not_converged:
+        _check(code, ctxs[0].handle if n else None)
+    out = []
+    for r in res:
+        d = {name: getattr(r, name) for name, _ in sdft_result._fields_}
+        d["status"] = code
+        out.append(d)
     return out
 
 

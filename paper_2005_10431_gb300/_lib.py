@@ -89,6 +89,7 @@ SIGNATURES = {
     "sdft_destroy": (None, [C.c_void_p]),
     "sdft_last_error": (C.c_char_p, [C.c_void_p]),
     "sdft_scf": (C.c_int, [C.c_void_p, C.POINTER(sdft_result)]),
+    "sdft_batch_scf": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(sdft_result)]),
     "sdft_reset": (C.c_int, [C.c_void_p]),
     "sdft_get_eigenvalues": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "sdft_get_occupations": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),

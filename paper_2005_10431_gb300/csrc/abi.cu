@@ -412,6 +412,30 @@ sdft_status sdft_scf(sdft_ctx* c, sdft_result* out) {
     }
 }
 
+sdft_status sdft_batch_scf(sdft_ctx* const* ctxs, int n, sdft_result* out) {
+    if (!ctxs || n < 1) return SDFT_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return SDFT_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) {
+                ctxs[i]->last_error = "a context appears twice in the batch";
+                return SDFT_ERR_INVALID_ARG;
+            }
+        ctxs[i]->last_error.clear();
+    }
+    try {
+        const sdft_status s = sdft::run_batch_scf(std::vector<sdft_ctx*>(ctxs, ctxs + n), out);
+        if (s == SDFT_ERR_NOT_CONVERGED)
+            for (int i = 0; i < n; ++i)
+                if (out && !out[i].converged)
+                    ctxs[i]->last_error = "SCF did not reach scf_tol within max_scf iterations";
+        return s;
+    } catch (const Error& e) {
+        for (int i = 1; i < n; ++i) ctxs[i]->last_error = e.msg;
+        return sdft::fail(ctxs[0], e);
+    }
+}
+
 sdft_status sdft_reset(sdft_ctx* c) { SDFT_TRY(c, { sdft::reset_state(c); SDFT_CUDA(cudaStreamSynchronize(c->stream)); }) }
 
 static sdft_status copy_out(sdft_ctx* c, const std::vector<double>& v, double* host, size_t n) {

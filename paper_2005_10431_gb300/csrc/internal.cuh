@@ -92,6 +92,8 @@ struct RowProblem {
     float phr[3], phi[3];
 };
 // one problem of a grouped KB projection C = gamma beta^H Y
+constexpr int MULTI_MAX = 64;   // cells per multi-cell filter launch
+
 struct KBProblem {
     const void* Y;
     void* C;
@@ -334,6 +336,7 @@ void rayleigh_ritz(sdft_ctx* c, int kpt, int precision, const void* Y, void* X, 
                    int ncol, const double* veff64, const float* veff32);
 void lanczos(sdft_ctx* c, int spin, int kpt, int steps, double* lower, double* upper);
 sdft_status run_scf(sdft_ctx* c, sdft_result* out);
+sdft_status run_batch_scf(const std::vector<sdft_ctx*>& ctxs, sdft_result* out);
 void reset_state(sdft_ctx* c);
 void seed_orbitals(sdft_ctx* c, int precision, bool cplx, void* X, int ncol, uint64_t seed);
 

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 
 namespace sdft {
 
@@ -300,13 +301,11 @@ void reset_state(sdft_ctx* c) {
     SDFT_CUDA(cudaGetLastError());
 }
 
-// one CheFSI pass of problem P at the current V_eff in `precision`
-static void chefsi_pass(sdft_ctx* c, Problem& P, int precision, void* X) {
+// Rayleigh-Ritz of problem P on the filtered block Y into X, and the new filter bounds
+static void rr_pass(sdft_ctx* c, Problem& P, int precision, void* Y, void* X) {
     const int ns = c->opt.nstates;
     const double* v64 = c->veff + (long long)P.spin * c->ng;
     const float* v32 = c->veff32 + (long long)P.spin * c->ng;
-    void* Y = c->blk[0];
-    chebyshev_filter(c, P.kpt, precision, X, Y, ns, c->opt.cheb_degree, P.cutoff, P.upper, P.lower, v64, v32);
     rayleigh_ritz(c, P.kpt, precision, Y, X, P.eig, ns, v64, v32);
     double e2[2];
     SDFT_CUDA(cudaMemcpyAsync(&e2[0], P.eig, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -315,6 +314,16 @@ static void chefsi_pass(sdft_ctx* c, Problem& P, int precision, void* X) {
     if (!std::isfinite(e2[0]) || !std::isfinite(e2[1])) throw Error{SDFT_ERR_NONFINITE, "Ritz values are not finite"};
     P.lower = e2[0];
     P.cutoff = e2[1];
+}
+
+// one CheFSI pass of problem P at the current V_eff in `precision`
+static void chefsi_pass(sdft_ctx* c, Problem& P, int precision, void* X) {
+    const double* v64 = c->veff + (long long)P.spin * c->ng;
+    const float* v32 = c->veff32 + (long long)P.spin * c->ng;
+    void* Y = c->blk[0];
+    chebyshev_filter(c, P.kpt, precision, X, Y, c->opt.nstates, c->opt.cheb_degree, P.cutoff, P.upper, P.lower, v64,
+                     v32);
+    rr_pass(c, P, precision, Y, X);
 }
 
 // ---- batched CheFSI: all problems of one storage kind in grouped launches -------------------
@@ -573,53 +582,67 @@ static void density_all(sdft_ctx* c, int precision, bool fp64_copy) {
     }
 }
 
-sdft_status run_scf(sdft_ctx* c, sdft_result* out) {
-    const long long ng = c->ng;
-    const int nsp = c->opt.nspin;
-    const long long nv = nsp * ng;
-    c->log.clear();
-    double* ftmp = c->work64 + 20 * ng;   // rho_tot + b
-    double* etmp = c->work64 + 21 * ng;   // two grid vectors for energies
-    double* diff = c->work64 + 18 * ng;   // rho_out - rho_in (2 ng)
-    double t_filter = 0, t_rr = 0, t_pois = 0;
-    const double t0 = now_s();
-    // device-side clock of the run: an event at the start and one at the end of each iteration
-    cudaEvent_t ev_start, ev_it;
-    SDFT_CUDA(cudaEventCreate(&ev_start));
-    SDFT_CUDA(cudaEventCreate(&ev_it));
-    SDFT_CUDA(cudaEventRecord(ev_start, c->stream));
-    struct EvGuard {
-        cudaEvent_t a, b;
-        ~EvGuard() {
-            cudaEventDestroy(a);
-            cudaEventDestroy(b);
-        }
-    } ev_guard{ev_start, ev_it};
-    bool converged = false;
+// One SCF run of a context, in stages, so that several contexts can be stepped in lockstep
+// (sdft_batch_scf) as well as alone (run_scf).
+struct ScfRun {
+    sdft_ctx* c;
+    long long ng = 0, nv = 0;
+    int nsp = 1, prec = SDFT_FP64;
+    double *ftmp = nullptr, *etmp = nullptr, *diff = nullptr;
+    double t_filter = 0, t_rr = 0, t_pois = 0, t0 = 0;
+    cudaEvent_t ev_start = nullptr, ev_it = nullptr;
+    bool converged = false, done = false;
     double last_err = 1.0;
-    int it = 0;
-    sdft_status status = SDFT_OK;
+    int it = 0, niter = 0;
     Energies E{};
-    const int prec = c->opt.precision;
     // batched CheFSI: problems of one storage kind that a grouped row-tile launch fits
     std::vector<Problem*> groups[2], single;
     int group_var[2] = {-1, -1};
     bool batched = false;
-    if (prec == SDFT_MIXED && c->opt.batch_problems && c->probs.size() > 1) {
-        for (int k = 0; k < 2; ++k) {
-            const int ncolE = k ? c->opt.nstates : c->opt.nstates / 2;
-            group_var[k] = group_variant_f32(c, k == 1, ncolE);
-        }
-        for (Problem& P : c->probs) {
-            const int k = P.cplx ? 1 : 0;
-            if (group_var[k] >= 0) groups[k].push_back(&P);
-            else single.push_back(&P);
-        }
-        batched = !groups[0].empty() || !groups[1].empty();
+
+    explicit ScfRun(sdft_ctx* c_) : c(c_) {}
+    ScfRun(const ScfRun&) = delete;
+    ScfRun& operator=(const ScfRun&) = delete;
+    ~ScfRun() {
+        if (ev_start) cudaEventDestroy(ev_start);
+        if (ev_it) cudaEventDestroy(ev_it);
     }
-    for (it = 0; it < c->opt.max_scf; ++it) {
-        // potentials from rho_in (paper Sec. 2.1: Poisson by AAR, then V_eff = phi + V_xc)
-        double ta = now_s();
+
+    int passes() const { return it == 0 ? std::max(1, c->opt.first_scf_filter_passes) : 1; }
+
+    void begin() {
+        ng = c->ng;
+        nsp = c->opt.nspin;
+        nv = nsp * ng;
+        prec = c->opt.precision;
+        c->log.clear();
+        ftmp = c->work64 + 20 * ng;   // rho_tot + b
+        etmp = c->work64 + 21 * ng;   // two grid vectors for energies
+        diff = c->work64 + 18 * ng;   // rho_out - rho_in (2 ng)
+        t0 = now_s();
+        // device-side clock of the run: an event at the start and one at the end of each iteration
+        SDFT_CUDA(cudaEventCreate(&ev_start));
+        SDFT_CUDA(cudaEventCreate(&ev_it));
+        SDFT_CUDA(cudaEventRecord(ev_start, c->stream));
+        if (prec == SDFT_MIXED && c->opt.batch_problems && c->probs.size() > 1) {
+            for (int k = 0; k < 2; ++k) {
+                const int ncolE = k ? c->opt.nstates : c->opt.nstates / 2;
+                group_var[k] = group_variant_f32(c, k == 1, ncolE);
+            }
+            for (Problem& P : c->probs) {
+                const int k = P.cplx ? 1 : 0;
+                if (group_var[k] >= 0) groups[k].push_back(&P);
+                else single.push_back(&P);
+            }
+            batched = !groups[0].empty() || !groups[1].empty();
+        }
+        done = c->opt.max_scf <= 0;
+    }
+
+    // potentials from rho_in (paper Sec. 2.1: Poisson by AAR, then V_eff = phi + V_xc), and the
+    // Lanczos bounds of problems that have none yet
+    void potential() {
+        const double ta = now_s();
         sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_in, nsp, c->b, ftmp, ng);
         count_launch(c);
         // the potential only needs to be as accurate as the current SCF error allows: a relative
@@ -633,35 +656,34 @@ sdft_status run_scf(sdft_ctx* c, sdft_result* out) {
         veff_assemble(c);
         SDFT_CUDA(cudaStreamSynchronize(c->stream));
         t_pois += now_s() - ta;
-        // CheFSI for every problem
         for (Problem& P : c->probs) {
-            if (!P.have_bounds) {
-                double lo, up;
-                lanczos(c, P.spin, P.kpt, c->opt.lanczos_steps, &lo, &up);
-                P.lower = lo;
-                P.upper = up;
-                P.cutoff = lo + 0.1 * (up - lo);
-                P.have_bounds = true;
-            }
-            if (batched) continue;   // passes run below, all problems together
-            const int passes = it == 0 ? std::max(1, c->opt.first_scf_filter_passes) : 1;
-            for (int p = 0; p < passes; ++p) {
-                ta = now_s();
-                chefsi_pass(c, P, prec, P.X);
-                t_filter += now_s() - ta;
-            }
+            if (P.have_bounds) continue;
+            double lo, up;
+            lanczos(c, P.spin, P.kpt, c->opt.lanczos_steps, &lo, &up);
+            P.lower = lo;
+            P.upper = up;
+            P.cutoff = lo + 0.1 * (up - lo);
+            P.have_bounds = true;
         }
-        if (batched) {
-            const int passes = it == 0 ? std::max(1, c->opt.first_scf_filter_passes) : 1;
-            for (int p = 0; p < passes; ++p) {
-                ta = now_s();
+    }
+
+    // this iteration's CheFSI passes of every problem of the context
+    void filter_all() {
+        const double ta = now_s();
+        for (int p = 0; p < passes(); ++p) {
+            if (batched) {
                 for (int k = 0; k < 2; ++k)
                     if (!groups[k].empty()) chefsi_pass_group(c, groups[k], group_var[k]);
                 for (Problem* P : single) chefsi_pass(c, *P, prec, P->X);
-                t_filter += now_s() - ta;
+            } else {
+                for (Problem& P : c->probs) chefsi_pass(c, P, prec, P.X);
             }
         }
-        // occupations, density, energy, error
+        t_filter += now_s() - ta;
+    }
+
+    // occupations, density, energy, error, log; Pulay update unless finished.  Returns done.
+    bool end_iteration() {
         fermi_device(c, c->probs[0].eig, c->probs[0].occ, c->scal + 8);
         density_all(c, prec, false);
         E = energy_hf(c, c->rho_in, c->veff, c->exc, c->phi, etmp);
@@ -690,78 +712,177 @@ sdft_status run_scf(sdft_ctx* c, sdft_result* out) {
         rec.cutoff = c->probs[0].cutoff;
         rec.upper = c->probs[0].upper;
         c->log.push_back(rec);
+        niter = it + 1;
         if (err < c->opt.scf_tol) {
             converged = true;
-            break;
+            done = true;
+            return true;
         }
         if (it + 1 < c->opt.max_scf) pulay_update(c);
+        ++it;
+        done = it >= c->opt.max_scf;
+        return done;
     }
-    const int niter = std::min(it + 1, c->opt.max_scf);
-    if (!converged) status = SDFT_ERR_NOT_CONVERGED;
-    // final FP64 pass for the mixed path, at the last V_eff
-    bool have64 = prec == SDFT_FP64;
-    if (prec == SDFT_MIXED && c->opt.final_fp64_pass) {
-        for (Problem& P : c->probs) {
-            convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, c->opt.nstates);
-            chefsi_pass(c, P, SDFT_FP64, P.X64);
+
+    sdft_status finish(sdft_result* out) {
+        const sdft_status status = converged ? SDFT_OK : SDFT_ERR_NOT_CONVERGED;
+        // final FP64 pass for the mixed path, at the last V_eff
+        bool have64 = prec == SDFT_FP64;
+        if (prec == SDFT_MIXED && c->opt.final_fp64_pass) {
+            for (Problem& P : c->probs) {
+                convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, c->opt.nstates);
+                chefsi_pass(c, P, SDFT_FP64, P.X64);
+            }
+            fermi_device(c, c->probs[0].eig, c->probs[0].occ, c->scal + 8);
+            density_all(c, SDFT_FP64, true);
+            E = energy_hf(c, c->rho_in, c->veff, c->exc, c->phi, etmp);
+            have64 = true;
         }
-        fermi_device(c, c->probs[0].eig, c->probs[0].occ, c->scal + 8);
-        density_all(c, SDFT_FP64, true);
-        E = energy_hf(c, c->rho_in, c->veff, c->exc, c->phi, etmp);
-        have64 = true;
+        // Kohn-Sham form at rho_out: phi[rho_out], eps_xc[rho_out]
+        double Fks = 0.0;
+        {
+            double* phi_o = c->work64 + 23 * ng;
+            double* exc_o = c->work64 + 24 * ng;
+            SDFT_CUDA(cudaMemcpyAsync(phi_o, c->phi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, c->stream));
+            sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_out, nsp, c->b, ftmp, ng);
+            count_launch(c);
+            const double ptol_o = std::min(c->opt.poisson_tol, 1e-2 * c->opt.scf_tol);
+            const int pit = prec == SDFT_MIXED ? poisson_mixed(c, ftmp, phi_o, ptol_o, 4000)
+                                               : poisson_aar(c, ftmp, phi_o, ptol_o, 4000);
+            if (pit < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Poisson AAR did not converge"};
+            double* vxc_o = c->work64 + 25 * ng;  // [nspin][ng]
+            lda_device(c, nsp, c->rho_out, exc_o, vxc_o, (size_t)ng);
+            sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_out, nsp, nullptr, etmp, ng);
+            sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_out, nsp, c->b, etmp + ng, ng);
+            count_launch(c, 2);
+            double vr, d[2];
+            const double* a1[1] = {c->veff};
+            const double* b1[1] = {c->rho_out};
+            dots_host(c, 1, a1, b1, nv, &vr);
+            const double* A[2] = {exc_o, etmp + ng};
+            const double* B[2] = {etmp, phi_o};
+            dots_host(c, 2, A, B, ng, d);
+            Fks = E.eband - c->dV * vr + c->dV * d[0] + 0.5 * c->dV * d[1] - c->E_self + c->E_sc + E.ts;
+        }
+        // results to host
+        const int ns = c->opt.nstates;
+        const size_t ne = c->probs.size() * ns;
+        c->eig_host.resize(ne);
+        c->occ_host.resize(ne);
+        SDFT_CUDA(cudaMemcpyAsync(c->eig_host.data(), c->probs[0].eig, sizeof(double) * ne, cudaMemcpyDeviceToHost,
+                                  c->stream));
+        SDFT_CUDA(cudaMemcpyAsync(c->occ_host.data(), c->probs[0].occ, sizeof(double) * ne, cudaMemcpyDeviceToHost,
+                                  c->stream));
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+        c->mu = E.mu;
+        c->ts = E.ts;
+        if (!have64)
+            for (Problem& P : c->probs) convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, ns);
+        forces_compute(c);
+        resolve_timing(c);
+        if (out) {
+            out->energy = E.F;
+            out->energy_ks = Fks;
+            out->mu = E.mu;
+            out->entropy_term = E.ts;
+            out->niter = niter;
+            out->converged = converged ? 1 : 0;
+            out->t_total = now_s() - t0;
+            out->t_filter = t_filter;
+            out->t_rr = t_rr;
+            out->t_poisson = t_pois;
+            out->t_other = out->t_total - t_filter - t_pois;
+        }
+        return status;
     }
-    // Kohn-Sham form at rho_out: phi[rho_out], eps_xc[rho_out]
-    double Fks = 0.0;
-    {
-        double* phi_o = c->work64 + 23 * ng;
-        double* exc_o = c->work64 + 24 * ng;
-        SDFT_CUDA(cudaMemcpyAsync(phi_o, c->phi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, c->stream));
-        sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_out, nsp, c->b, ftmp, ng);
-        count_launch(c);
-        const double ptol_o = std::min(c->opt.poisson_tol, 1e-2 * c->opt.scf_tol);
-        const int pit = prec == SDFT_MIXED ? poisson_mixed(c, ftmp, phi_o, ptol_o, 4000)
-                                           : poisson_aar(c, ftmp, phi_o, ptol_o, 4000);
-        if (pit < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Poisson AAR did not converge"};
-        double* vxc_o = c->work64 + 25 * ng;  // [nspin][ng]
-        lda_device(c, nsp, c->rho_out, exc_o, vxc_o, (size_t)ng);
-        sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_out, nsp, nullptr, etmp, ng);
-        sum_spins_kernel<<<nb(ng), 256, 0, c->stream>>>(c->rho_out, nsp, c->b, etmp + ng, ng);
-        count_launch(c, 2);
-        double vr, d[2];
-        const double* a1[1] = {c->veff};
-        const double* b1[1] = {c->rho_out};
-        dots_host(c, 1, a1, b1, nv, &vr);
-        const double* A[2] = {exc_o, etmp + ng};
-        const double* B[2] = {etmp, phi_o};
-        dots_host(c, 2, A, B, ng, d);
-        Fks = E.eband - c->dV * vr + c->dV * d[0] + 0.5 * c->dV * d[1] - c->E_self + c->E_sc + E.ts;
+};
+
+sdft_status run_scf(sdft_ctx* c, sdft_result* out) {
+    ScfRun r(c);
+    r.begin();
+    while (!r.done) {
+        r.potential();
+        r.filter_all();
+        r.end_iteration();
     }
-    // results to host
-    const int ns = c->opt.nstates;
-    const size_t ne = c->probs.size() * ns;
-    c->eig_host.resize(ne);
-    c->occ_host.resize(ne);
-    SDFT_CUDA(cudaMemcpyAsync(c->eig_host.data(), c->probs[0].eig, sizeof(double) * ne, cudaMemcpyDeviceToHost, c->stream));
-    SDFT_CUDA(cudaMemcpyAsync(c->occ_host.data(), c->probs[0].occ, sizeof(double) * ne, cudaMemcpyDeviceToHost, c->stream));
-    SDFT_CUDA(cudaStreamSynchronize(c->stream));
-    c->mu = E.mu;
-    c->ts = E.ts;
-    if (!have64)
-        for (Problem& P : c->probs) convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, ns);
-    forces_compute(c);
-    resolve_timing(c);
-    if (out) {
-        out->energy = E.F;
-        out->energy_ks = Fks;
-        out->mu = E.mu;
-        out->entropy_term = E.ts;
-        out->niter = niter;
-        out->converged = converged ? 1 : 0;
-        out->t_total = now_s() - t0;
-        out->t_filter = t_filter;
-        out->t_rr = t_rr;
-        out->t_poisson = t_pois;
-        out->t_other = out->t_total - t_filter - t_pois;
+    return r.finish(out);
+}
+
+// Several contexts' SCFs in lockstep.  Each iteration: the potentials of every running context,
+// then the CheFSI passes, where the cells that the multi-cell filter takes (mixed precision, one
+// real Gamma-point problem, one shared stream, the same degree and pass count) are filtered
+// together -- one grouped KB projection and one stencil launch per Chebyshev step for all of
+// them -- followed by each cell's Rayleigh-Ritz; then every context's density, energy and mixing.
+// A context leaves the lockstep when it converges or reaches its max_scf.  The results are
+// those of running each context alone with the column-tile stencil.
+sdft_status run_batch_scf(const std::vector<sdft_ctx*>& ctxs, sdft_result* out) {
+    const int n = (int)ctxs.size();
+    std::vector<std::unique_ptr<ScfRun>> runs;
+    for (sdft_ctx* c : ctxs) runs.emplace_back(new ScfRun(c));
+    for (auto& r : runs) r->begin();
+    auto multi_ok = [&](const ScfRun& r) {
+        const sdft_ctx* c = r.c;
+        return r.prec == SDFT_MIXED && c->probs.size() == 1 && !c->probs[0].cplx && c->stream == ctxs[0]->stream;
+    };
+    for (;;) {
+        std::vector<ScfRun*> live;
+        for (auto& r : runs)
+            if (!r->done) live.push_back(r.get());
+        if (live.empty()) break;
+        for (ScfRun* r : live) r->potential();
+        // cells for the multi-cell filter, grouped by (degree, passes), at most MULTI_MAX per launch
+        std::vector<ScfRun*> rest;
+        std::vector<std::vector<ScfRun*>> sets;
+        for (ScfRun* r : live) {
+            if (!multi_ok(*r)) {
+                rest.push_back(r);
+                continue;
+            }
+            bool placed = false;
+            for (auto& g : sets)
+                if (g.size() < (size_t)MULTI_MAX && g[0]->c->opt.cheb_degree == r->c->opt.cheb_degree &&
+                    g[0]->passes() == r->passes()) {
+                    g.push_back(r);
+                    placed = true;
+                    break;
+                }
+            if (!placed) sets.push_back({r});
+        }
+        for (auto& g : sets) {
+            if (g.size() == 1) {
+                rest.push_back(g[0]);
+                continue;
+            }
+            const double ta = now_s();
+            std::vector<sdft_ctx*> cs;
+            std::vector<const void*> xs;
+            std::vector<void*> ys;
+            for (ScfRun* r : g) {
+                cs.push_back(r->c);
+                xs.push_back(r->c->probs[0].X);
+                ys.push_back(r->c->blk[0]);
+            }
+            std::vector<double> a(g.size()), b(g.size()), a0(g.size());
+            for (int p = 0; p < g[0]->passes(); ++p) {
+                for (size_t i = 0; i < g.size(); ++i) {
+                    const Problem& P = g[i]->c->probs[0];
+                    a[i] = P.cutoff;
+                    b[i] = P.upper;
+                    a0[i] = P.lower;
+                }
+                chebyshev_filter_multi(cs, xs, ys, g[0]->c->opt.cheb_degree, a.data(), b.data(), a0.data());
+                for (ScfRun* r : g) rr_pass(r->c, r->c->probs[0], SDFT_MIXED, r->c->blk[0], r->c->probs[0].X);
+            }
+            const double share = (now_s() - ta) / (double)g.size();
+            for (ScfRun* r : g) r->t_filter += share;
+        }
+        for (ScfRun* r : rest) r->filter_all();
+        for (ScfRun* r : live) r->end_iteration();
+    }
+    sdft_status status = SDFT_OK;
+    for (int i = 0; i < n; ++i) {
+        const sdft_status s = runs[i]->finish(out ? out + i : nullptr);
+        if (s != SDFT_OK && status == SDFT_OK) status = s;
     }
     return status;
 }

@@ -392,7 +392,6 @@ cheb_step_kernel(const E* __restrict__ Y, const E* __restrict__ Yprev, E* __rest
 }
 
 // ---- several grids in one launch (independent cells of uneven size, FP32 real blocks) -----
-constexpr int MULTI_MAX = 64;
 }  // namespace
 struct MultiProblem {                 // one cell's block in a multi-grid launch of the column tile
     StepArgs<float> A;                // grid, coefficients, recurrence step, z chunking

@@ -62,3 +62,43 @@ def test_multi_cell_filter_rejects_complex_and_fp64(sd):
     x = torch.zeros((c.nstates, c.ngrid), dtype=torch.float64, device="cuda")
     with pytest.raises(sd.SdftError):
         sd.sdft_chebyshev_filter_multi([ctx], [x], [torch.empty_like(x)], 4, [2.0], [90.0], [-1.0])
+
+
+def test_batch_scf_matches_cell_by_cell(sd, monkeypatch):
+    """sdft_batch_scf over four uneven cells (multi-cell filter) and one FP64 context (filtered on
+    its own inside the lockstep): every context's SCF is bitwise the one it runs alone with the
+    same stencil tile -- same iteration count, energies and eigenvalues."""
+    monkeypatch.setenv("SDFT_STENCIL_VARIANT", "0")   # the column tile the multi-cell launch uses
+    cells = workloads.uneven_cells(count=4, seed=5)
+    specs = [(c, sd.SDFT_MIXED) for c in cells] + [(cells[0], sd.SDFT_FP64)]
+
+    def make(c, prec):
+        return sd.sdft_create(c.L, c.n, c.pos, c.types, c.species,
+                              dict(nstates=c.nstates, precision=prec, scf_tol=1e-6, max_scf=30))
+
+    alone = []
+    for c, prec in specs:
+        ctx = make(c, prec)
+        r = sd.sdft_scf(ctx)
+        alone.append((r, sd.sdft_get_eigenvalues(ctx), sd.sdft_get_forces(ctx)))
+        sd.sdft_destroy(ctx)
+    ctxs = [make(c, prec) for c, prec in specs]
+    rs = sd.sdft_batch_scf(ctxs)
+    for i, (r, eig, frc) in enumerate(alone):
+        assert rs[i]["niter"] == r["niter"]
+        assert rs[i]["converged"] == r["converged"]
+        assert rs[i]["energy"] == r["energy"]
+        assert rs[i]["energy_ks"] == r["energy_ks"]
+        assert np.array_equal(sd.sdft_get_eigenvalues(ctxs[i]), eig)
+        assert np.array_equal(sd.sdft_get_forces(ctxs[i]), frc)
+    for ctx in ctxs:
+        sd.sdft_destroy(ctx)
+
+
+def test_batch_scf_rejects_repeated_context(sd):
+    c = workloads.uneven_cells(count=1, seed=5)[0]
+    ctx = sd.sdft_create(c.L, c.n, c.pos, c.types, c.species, dict(nstates=c.nstates, precision=sd.SDFT_MIXED))
+    with pytest.raises(sd.SdftError) as e:
+        sd.sdft_batch_scf([ctx, ctx])
+    assert e.value.code == -1
+    sd.sdft_destroy(ctx)
