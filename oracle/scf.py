@@ -140,17 +140,19 @@ class Problem:
         return F
 
 
-def initial_blocks(cell, seed=None):
-    """Starting orbitals for every (spin, k) problem from the shared counter-based generator."""
+def initial_blocks(cell, seed=None, nvec=None):
+    """Starting orbitals for every (spin, k) problem from the shared counter-based generator
+    (nvec rows, default nstates; the first nstates rows do not depend on nvec)."""
     kpts, _ = cell.kpoints()
     seed = cell.seed if seed is None else seed
+    nvec = cell.nstates if nvec is None else nvec
     out = []
     for s in range(cell.nspin):
         row = []
         for ik in range(kpts.shape[0]):
             cplx = bool(np.any(kpts[ik] != 0))
             row.append(workloads.initial_orbitals(problem_seed(seed, s, ik, kpts.shape[0]),
-                                                  cell.ngrid, cell.nstates, cplx))
+                                                  cell.ngrid, nvec, cplx))
         out.append(row)
     return out
 
@@ -169,17 +171,34 @@ def initial_density(cell, rho0=None, moment=0.125):
 
 def scf(cell, max_iter=100, tol=None, mix_beta=0.3, mix_hist=7, pulay_period=1, pulay_restart=False,
         first_passes=4, rho0=None, blocks=None, lanczos_steps=20, final_tol=None, final_max_passes=60,
-        with_forces=False, verbose=False, ref_energy=None):
+        with_forces=False, verbose=False, ref_energy=None, nbuffer=0, degree=None, kerker_k0=None):
     """SCF fixed point on the density with CheFSI (Sec. 2.1).
 
     final_tol: if given, after density convergence keep doing CheFSI passes at the final
-    V_eff until max |H x - lambda x| < final_tol (used for tight parity references)."""
+    V_eff until max |H x - lambda x| < final_tol (used for tight parity references).
+
+    Solver choices that leave the fixed point unchanged (the self-consistent density built from
+    the lowest nstates eigenpairs of H[rho] with Fermi-Dirac occupations over those nstates):
+      nbuffer    extra filtered vectors that are never occupied.  The filter cutoff becomes the
+                 top Ritz value of the larger block, so the partially occupied states at the top
+                 of the nstates block are no longer next to the cutoff, where the Chebyshev
+                 filter barely separates them (Zhou et al. 2006 use such buffer states too);
+      degree     Chebyshev degree (default: the cell's);
+      kerker_k0  if given, Kerker-preconditioned periodic Pulay mixing (oracle.kerker, Sec. 2.1
+                 preconditioned mixing) with this screening wavevector instead of plain Pulay."""
     tol = cell.scf_tol if tol is None else tol
     pr = Problem(cell)
     nk = pr.kpts.shape[0]
+    ns = cell.nstates
+    degree = cell.cheb_degree if degree is None else int(degree)
     rho_in = initial_density(cell, rho0)
-    blocks = initial_blocks(cell) if blocks is None else blocks
-    mixer = PulayMixer(mix_beta, mix_hist, pulay_period, pulay_restart)
+    blocks = initial_blocks(cell, nvec=ns + nbuffer) if blocks is None else blocks
+    if kerker_k0 is None:
+        mixer = PulayMixer(mix_beta, mix_hist, pulay_period, pulay_restart)
+    else:
+        from .kerker import KerkerPulayMixer
+        mixer = KerkerPulayMixer(cell, kerker_k0, mix_beta, mix_hist, pulay_period, pulay_restart,
+                                 nchan=cell.nspin)
     bounds = {}
     hist = []
     t0 = time.time()
@@ -196,12 +215,12 @@ def scf(cell, max_iter=100, tol=None, mix_beta=0.3, mix_hist=7, pulay_period=1, 
                     bounds[s, ik] = [lo, lo + 0.1 * (up - lo), up]
                 for _ in range(first_passes if it == 0 else 1):
                     a0, a, b = bounds[s, ik]
-                    lam, blocks[s][ik] = chefsi.chefsi_pass(H, blocks[s][ik], cell.cheb_degree, a, b, a0)
+                    lam, blocks[s][ik] = chefsi.chefsi_pass(H, blocks[s][ik], degree, a, b, a0)
                     bounds[s, ik] = [lam[0], lam[-1], b]
-                eigs[s, ik] = lam
+                eigs[s, ik] = lam[:ns]
         mu, occ = ham.fermi_occupations(eigs, pr.kw, cell.nelec, cell.kT, pr.spin_factor)
         ts = ham.entropy_term(occ, pr.kw, cell.kT, pr.spin_factor)
-        rho_out = ham.density(blocks, occ, pr.kw, pr.dV)
+        rho_out = ham.density(_lowest(blocks, ns), occ, pr.kw, pr.dV)
         F = pr.free_energy_hf(eigs, occ, rho_in, veff, phi, exc, ts)
         err = float(np.linalg.norm(rho_out - rho_in) / np.linalg.norm(rho_out))
         hist.append(dict(iter=it, energy=F, err=err, mu=mu, t=time.time() - t0))
@@ -218,9 +237,9 @@ def scf(cell, max_iter=100, tol=None, mix_beta=0.3, mix_hist=7, pulay_period=1, 
                 for ik in range(nk):
                     H = pr.apply_h(veff[s], ik)
                     a0, a, b = bounds[s, ik]
-                    lam, blocks[s][ik] = chefsi.chefsi_pass(H, blocks[s][ik], cell.cheb_degree, a, b, a0)
+                    lam, blocks[s][ik] = chefsi.chefsi_pass(H, blocks[s][ik], degree, a, b, a0)
                     bounds[s, ik] = [lam[0], lam[-1], b]
-                    eigs[s, ik] = lam
+                    eigs[s, ik] = lam[:ns]
                     nocc = int(np.sum(occ[s, ik] > 1e-12 * pr.spin_factor)) + 1
                     res = chefsi.residual_norms(H, blocks[s][ik][:nocc], lam[:nocc])
                     worst = max(worst, float(res.max()))
@@ -228,10 +247,16 @@ def scf(cell, max_iter=100, tol=None, mix_beta=0.3, mix_hist=7, pulay_period=1, 
                 break
         mu, occ = ham.fermi_occupations(eigs, pr.kw, cell.nelec, cell.kT, pr.spin_factor)
         ts = ham.entropy_term(occ, pr.kw, cell.kT, pr.spin_factor)
-        rho_out = ham.density(blocks, occ, pr.kw, pr.dV)
+        rho_out = ham.density(_lowest(blocks, ns), occ, pr.kw, pr.dV)
         F = pr.free_energy_hf(eigs, occ, rho_in, veff, phi, exc, ts)
     Fks = pr.free_energy_ks(eigs, occ, rho_out, veff, ts)
+    blocks = _lowest(blocks, ns)
     res = SCFResult(F, Fks, eigs, occ, mu, rho_out, phi, veff, blocks, it + 1, hist, converged)
     if with_forces:
         res.forces = pr.forces(blocks, occ, phi)
     return res
+
+
+def _lowest(blocks, ns):
+    """The lowest ns Ritz vectors of every (spin, k) block (buffer vectors dropped)."""
+    return [[X[:ns] for X in row] for row in blocks]

@@ -184,3 +184,25 @@ def test_chebyshev_filter_matches_closed_form_polynomial():
     p = T((lam - cc) / e) / T(np.array([(a0 - cc) / e]))[0]
     ref = (Q @ (p[:, None] * (Q.T @ X.T))).T
     assert np.max(np.abs(Y - ref)) < 1e-10 * np.max(np.abs(ref))
+
+
+def test_entropy_term_equals_grand_potential_identity_at_finite_temperature():
+    # Fermi-Dirac occupations g = f_s f(x), x = (lambda - mu)/kT, satisfy, eigenvalue by eigenvalue,
+    #   f ln f + (1 - f) ln(1 - f) = -ln(1 + e^-x) - f x,
+    # so at fixed eigenvalues the Mermin term is
+    #   -TS = -kT f_s sum_k w_k sum_n ln(1 + e^-x) - sum_k w_k sum_n g (lambda - mu)
+    # (the grand potential of the occupied levels minus their band energy relative to mu).  This pins
+    # the prefactor and sign of entropy_term at finite kT, where every candidate formula differs.
+    rng = np.random.default_rng(5)
+    for nspin, fs in ((1, 2.0), (2, 1.0)):
+        eigs = np.sort(rng.normal(0.0, 0.05, size=(nspin, 3, 20)), axis=-1)
+        kw = np.array([0.5, 0.3, 0.2])
+        for kT in (0.002, 0.01, 0.03):
+            nelec = 0.6 * fs * 20 * nspin / (2.0 if nspin == 1 else 1.0)
+            mu, g = ham.fermi_occupations(eigs, kw, nelec, kT, fs)
+            x = (eigs - mu) / kT
+            wk = kw[None, :, None]
+            ref = -kT * fs * np.sum(wk * np.logaddexp(0.0, -x)) - np.sum(wk * g * (eigs - mu))
+            got = ham.entropy_term(g, kw, kT, fs)
+            assert abs(got - ref) < 1e-13 * max(1.0, abs(ref)), (nspin, kT, got, ref)
+            assert got < 0.0   # -TS is negative for fractional occupations
