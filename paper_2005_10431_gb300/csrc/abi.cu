@@ -548,6 +548,7 @@ sdft_status sdft_apply_h(sdft_ctx* c, int spin, int kpt, int precision, const vo
         sdft::apply_h(c, kpt, precision, x, y, ncol, c->veff + (long long)spin * c->ng,
                       c->veff32 + (long long)spin * c->ng);
         SDFT_CUDA(cudaStreamSynchronize(c->stream));
+        sdft::check_stencil_flag(c);
     })
 }
 
@@ -559,6 +560,7 @@ sdft_status sdft_chebyshev_filter(sdft_ctx* c, int spin, int kpt, int precision,
         sdft::chebyshev_filter(c, kpt, precision, x, y, ncol, degree, a, b, a0, c->veff + (long long)spin * c->ng,
                                c->veff32 + (long long)spin * c->ng);
         SDFT_CUDA(cudaStreamSynchronize(c->stream));
+        sdft::check_stencil_flag(c);
     })
 }
 

@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(256, 1)
 gram_tc_kernel(const float* __restrict__ Y, const float* __restrict__ HY, int ncol, long long ng, long long chunk,
                const TilePair* __restrict__ pairs, float* __restrict__ part, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // align by offsetting the array itself (not through an integer cast): accesses stay shared-memory ones
+    unsigned char* smem = smem_raw + ((1024u - ((unsigned)__cvta_generic_to_shared(smem_raw) & 1023u)) & 1023u);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);   // one per stage
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NSTAGE);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -231,7 +232,10 @@ gram_tc_kernel(const float* __restrict__ Y, const float* __restrict__ HY, int nc
         unsigned char *b_lo = st + 4 * TILE_BYTES, *c_lo = st + 5 * TILE_BYTES;
         // the MMAs that read this stage two tiles ago must be complete before it is refilled
         if (t >= NSTAGE) {
-            if (!mbar_wait(&bars[s], (uint32_t)(((t - NSTAGE) / NSTAGE) & 1))) {
+            // the outcome is made block-uniform, so that every thread takes the same path through the
+            // barriers below (a thread that timed out must not leave while others wait for it)
+            const bool waited = mbar_wait(&bars[s], (uint32_t)(((t - NSTAGE) / NSTAGE) & 1));
+            if (!__syncthreads_and(waited)) {
                 ok = false;
                 break;
             }
@@ -264,11 +268,9 @@ gram_tc_kernel(const float* __restrict__ Y, const float* __restrict__ HY, int nc
             const int s = t % NSTAGE;
             if (!mbar_wait(&bars[s], (uint32_t)((t / NSTAGE) & 1))) ok = false;
         }
-    } else if (threadIdx.x == 0) {
-        atomicExch(err, 1);
     }
     fence_after_sync();
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;   // block-uniform: the error path below is taken by all threads or none
     if (!ok) {
         if (threadIdx.x == 0) atomicExch(err, 1);
         // bounded second wait for MMAs still in flight before the tensor memory is released
@@ -342,7 +344,8 @@ __global__ void __launch_bounds__(256, 1)
 rotate_tc_kernel(const float* __restrict__ Y, const float* __restrict__ Q32, float* __restrict__ X, int ncol,
                  long long ng, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // align by offsetting the array itself (not through an integer cast): accesses stay shared-memory ones
+    unsigned char* smem = smem_raw + ((1024u - ((unsigned)__cvta_generic_to_shared(smem_raw) & 1023u)) & 1023u);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NSTAGE * ROT_STAGE_BYTES);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NSTAGE);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -397,7 +400,10 @@ rotate_tc_kernel(const float* __restrict__ Y, const float* __restrict__ Q32, flo
         unsigned char* st = smem + s * ROT_STAGE_BYTES;
         unsigned char *a_hi = st, *a_lo = st + TILE_BYTES, *b_hi = st + 2 * TILE_BYTES, *b_lo = st + 3 * TILE_BYTES;
         if (t >= NSTAGE) {
-            if (!mbar_wait(&bars[s], (uint32_t)(((t - NSTAGE) / NSTAGE) & 1))) {
+            // the outcome is made block-uniform, so that every thread takes the same path through the
+            // barriers below (a thread that timed out must not leave while others wait for it)
+            const bool waited = mbar_wait(&bars[s], (uint32_t)(((t - NSTAGE) / NSTAGE) & 1));
+            if (!__syncthreads_and(waited)) {
                 ok = false;
                 break;
             }
@@ -452,7 +458,7 @@ rotate_tc_kernel(const float* __restrict__ Y, const float* __restrict__ Q32, flo
         }
     }
     fence_after_sync();
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;   // block-uniform: the error path below is taken by all threads or none
     if (!ok) {
         if (threadIdx.x == 0) atomicExch(err, 1);
         for (int s = 0; s < NSTAGE; ++s)
@@ -485,7 +491,7 @@ rotate_tc_kernel(const float* __restrict__ Y, const float* __restrict__ Q32, flo
 
 }  // namespace
 
-bool rotate_tc_supported(int precision, bool cplx, int ncol) { return gram_tc_supported(precision, cplx, ncol); }
+
 
 // X = Y Q for FP32 paired blocks; Q32 is Q in FP32, column-major ncol x ncol
 void rotate_tc(sdft_ctx* c, const void* Y, const float* Q32, void* X, int ncol) {
@@ -507,9 +513,16 @@ void rotate_tc(sdft_ctx* c, const void* Y, const float* Q32, void* X, int ncol) 
 namespace {
 }  // namespace
 
-bool gram_tc_supported(int precision, bool cplx, int ncol) {
+static bool tc_block_ok(int precision, bool cplx, int ncol) {
     return precision == SDFT_MIXED && !cplx && ncol >= 32 && ncol % 2 == 0 && getenv("SDFT_NO_TCGEN05") == nullptr;
 }
+// the Gram's tile-pair table holds at most 64 pairs (10 tiles of 128 columns); wider blocks use the
+// CUDA-core Gram
+bool gram_tc_supported(int precision, bool cplx, int ncol) {
+    const int tiles = (ncol + TC_M - 1) / TC_M;
+    return tc_block_ok(precision, cplx, ncol) && tiles * (tiles + 1) / 2 <= 64;
+}
+bool rotate_tc_supported(int precision, bool cplx, int ncol) { return tc_block_ok(precision, cplx, ncol); }
 
 void subspace_gram_tc(sdft_ctx* c, const void* Y, const void* HY, double* M, double* Hs, int ncol) {
     const int tiles = (ncol + TC_M - 1) / TC_M;

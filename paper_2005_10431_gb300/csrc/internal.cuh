@@ -284,6 +284,18 @@ void launch_cheb_step<float>(sdft_ctx* c, int kpt, const float* Y, const float* 
 template <typename E>
 void launch_kb_project(sdft_ctx* c, int kpt, const E* Y, E* C, int ncolE);
 
+// ---- stencil_tma.cu: TMA-fed slab tile (FP32 real paired blocks) -----------------------
+template <int N1, int TY, int NP, int S, int D>
+bool slab_variant_ok(const sdft_ctx* c, int ncolE);
+template <int N1, int TY, int NP, int RY, int S, int D, int MINB>
+void launch_slab_variant(sdft_ctx* c, int kpt, const float2* Y, const float2* Yprev, float2* Ynext, int ncolE,
+                         const float* V, const float2* kbC, double alpha, double beta, double shift, bool kin,
+                         bool timed);
+// sticky device flag (int) set by a stencil launch whose bounded mbarrier wait gave up
+int* stencil_error_flag(sdft_ctx* c);
+// throws SDFT_ERR_DEVICE_TIMEOUT if that flag is set (reads it after the stream's work so far)
+void check_stencil_flag(sdft_ctx* c);
+
 // ---- kb.cu ---------------------------------------------------------------------------
 void build_kb_tables(sdft_ctx* c, int kpt);
 

@@ -311,6 +311,7 @@ static void rr_pass(sdft_ctx* c, Problem& P, int precision, void* Y, void* X) {
     SDFT_CUDA(cudaMemcpyAsync(&e2[0], P.eig, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     SDFT_CUDA(cudaMemcpyAsync(&e2[1], P.eig + ns - 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    check_stencil_flag(c);
     if (!std::isfinite(e2[0]) || !std::isfinite(e2[1])) throw Error{SDFT_ERR_NONFINITE, "Ritz values are not finite"};
     P.lower = e2[0];
     P.cutoff = e2[1];

@@ -25,6 +25,13 @@ const StepVariant<float2> kReal[] = {
     {&launch_row_variant<false, 8, 1, 512, 1, 3>, &row_ok<8, 512, 3>, "row8", &launch_row_group<false, 8, 1, 512, 1, 3>},
     {&launch_row_variant<false, 5, 2, 320, 1, 3>, &row_ok<5, 320, 3>, "row5", &launch_row_group<false, 5, 2, 320, 1, 3>},
     {&launch_row_variant<false, 6, 2, 384, 1, 3>, &row_ok<6, 384, 3>, "row6", &launch_row_group<false, 6, 2, 384, 1, 3>},
+    // TMA-fed slab tiles (stencil_tma.cu): (n1, TY rows, NP pairs, RY rows per thread, KB slots, stages,
+    // min blocks per SM)
+    {&launch_slab_variant<80, 8, 2, 1, 2, 3, 1>, &slab_variant_ok<80, 8, 2, 2, 3>, "slab80"},
+    {&launch_slab_variant<80, 8, 1, 1, 2, 4, 1>, &slab_variant_ok<80, 8, 1, 2, 4>, "slab80np1"},
+    {&launch_slab_variant<120, 8, 1, 1, 2, 4, 1>, &slab_variant_ok<120, 8, 1, 2, 4>, "slab120"},
+    {&launch_slab_variant<40, 8, 2, 1, 2, 4, 1>, &slab_variant_ok<40, 8, 2, 2, 4>, "slab40"},
+    {&launch_slab_variant<80, 8, 1, 2, 2, 4, 1>, &slab_variant_ok<80, 8, 1, 2, 4>, "slab80ry2"},
 };
 const StepVariant<float2> kCplx[] = {
     {&launch_variant<float2, true, 32, 8, 2, 2, 4>, nullptr, "col32x8"},

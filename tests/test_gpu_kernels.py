@@ -124,6 +124,58 @@ def test_every_stencil_tile_variant_matches_oracle(sd, variant, cplx, monkeypatc
     assert _relerr(sd.unpack_block(y, sd.SDFT_MIXED, cplx), ref) < 3e-5 * 4
 
 
+# TMA-fed slab tiles (real FP32 blocks): variant index in the real table, grid, and a cell whose KB
+# spheres overlap in pairs but never three at a point (the tile stages two KB slots per point).
+# n2 = 24 gives slabs at the lower periodic y boundary, in the interior and at the upper boundary;
+# n3 = 40 gives several z chunks with a ragged last one; 6 states = 3 pairs, a ragged pair group.
+SLAB_VARIANTS = [(11, "slab80", (80, 24, 40)), (12, "slab80np1", (80, 24, 40)), (13, "slab120", (120, 24, 30)),
+                 (14, "slab40", (40, 24, 40)), (15, "slab80ry2", (80, 24, 40))]
+
+
+def _slab_cell(n):
+    h = 0.3
+    c = workloads.small_cell(npts=10, L=4.0, natom=3, seed=21, nstates=6)
+    c.n = n
+    c.L = tuple(h * k for k in n)
+    c.pos = np.array([[3.0, 2.0, 1.5], [6.5, 4.5, 4.0], [9.5, 5.5, 5.0]]) if n[0] == 40 else \
+        np.array([[3.0, 2.0, 1.5], [6.5, 4.5, 4.0], [16.0, 3.0, 3.0]])
+    c.types = np.zeros(3, int)
+    return c
+
+
+@pytest.mark.parametrize("variant,name,n", SLAB_VARIANTS)
+def test_slab_stencil_variants_match_oracle(sd, variant, name, n, monkeypatch):
+    monkeypatch.setenv("SDFT_STENCIL_VARIANT", str(variant))
+    cell = _slab_cell(n)
+    ns = 6
+    ctx = _ctx(sd, cell, sd.SDFT_MIXED, ns)
+    V = np.random.default_rng(17).normal(0, 0.4, cell.ngrid)
+    sd.sdft_set_veff(ctx, 0, V)
+    X = workloads.initial_orbitals(19, cell.ngrid, ns)
+    x = sd.pack_block(X, sd.SDFT_MIXED)
+    y = torch.empty_like(x)
+    P = model.projectors(cell)
+    E = model.kb_energies(cell)
+    # one H X (no recurrence term), then a degree-4 filter (with the Yprev term)
+    sd.sdft_apply_h(ctx, 0, 0, sd.SDFT_MIXED, x, y, ns)
+    assert sd.sdft_get_stencil_variant(ctx, False) == (variant, name)
+    ref = ham.apply_h(cell, X, V, P, E)
+    assert _relerr(sd.unpack_block(y, sd.SDFT_MIXED, False), ref) < 2e-5
+    sd.sdft_chebyshev_filter(ctx, 0, 0, sd.SDFT_MIXED, x, y, ns, 4, 3.0, 90.0, -1.5)
+    assert sd.sdft_get_stencil_variant(ctx, False) == (variant, name)
+    ref = chefsi.chebyshev_filter(lambda Z: ham.apply_h(cell, Z, V, P, E), X, 4, 3.0, 90.0, -1.5)
+    assert _relerr(sd.unpack_block(y, sd.SDFT_MIXED, False), ref) < 3e-5 * 4
+
+
+def test_slab_cell_has_at_most_two_kb_slots():
+    # the slab test cells must stay within the tile's two staged KB slots per point
+    for _, _, n in SLAB_VARIANTS:
+        cell = _slab_cell(n)
+        P = model.projectors(cell)
+        per_point = np.asarray((P != 0).sum(axis=0)).ravel()
+        assert per_point.max() <= 2
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_chebyshev_filter_matches_oracle(sd, precision):
     cell = _ragged_cell()
