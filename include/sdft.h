@@ -113,6 +113,10 @@ typedef struct {
     int use_graphs;            /* 1: the grouped filter of a batched pass (table upload, m KB projections
                                   and stencil steps, and the H Y of Rayleigh-Ritz) is captured once as a
                                   CUDA graph and replayed every pass (not while kernel timing is on) */
+    double kerker_k0;          /* > 0: Kerker-preconditioned Pulay mixing (paper Sec. 2.1, preconditioned
+                                  periodic Pulay) with screening wavevector k0 (1/bohr): the linear part of
+                                  every update is P(beta r), P = (-L_h)(-L_h + k0^2)^-1 applied channel by
+                                  channel through a screened-Poisson AAR solve; 0: plain Pulay */
 } sdft_options;
 
 /* Per-iteration record of the SCF (paper Sec. 2.1 ".out" progress). */
@@ -284,6 +288,22 @@ sdft_status sdft_poisson(sdft_ctx* ctx, const double* f, double* phi, double tol
 /* Perdew-Zunger LDA (paper Sec. 3): rho [nspin][n] -> eps_xc [n], v_xc [nspin][n]; device FP64. */
 sdft_status sdft_lda(sdft_ctx* ctx, int nspin, const double* rho, double* exc, double* vxc,
                      size_t n);
+
+/* Kerker preconditioner of the density mixing (paper Sec. 2.1): out = P f = f - k0^2 y with
+ * (-L_h + k0^2) y = f solved by AAR (FP64, Jacobi-preconditioned Richardson steps with Anderson
+ * extrapolation) to a relative residual of tol, for nchan channels of ngrid points each (device FP64,
+ * [nchan][ngrid]; f and out may not overlap).  On a plane wave of FD eigenvalue -lambda this multiplies
+ * by lambda / (lambda + k0^2): the uniform component is removed and short waves pass.  k0 > 0, tol > 0.
+ * NOT_CONVERGED if the solve does not reach tol in max_iter iterations. */
+sdft_status sdft_kerker(sdft_ctx* ctx, const double* f, double* out, int nchan, double k0, double tol,
+                        int max_iter);
+
+/* One step of the context's density mixer (paper Sec. 2.1: periodic Pulay, Kerker-preconditioned when
+ * opt.kerker_k0 > 0), exactly as sdft_scf applies it between iterations: from the input density x_in and
+ * the output density x_out ([nspin][ngrid], device FP64) it pushes the history and writes the next input
+ * x_next (device, may alias neither x_in nor x_out).  The history is the context's own: sdft_reset clears
+ * it, and sdft_scf uses and then clears it. */
+sdft_status sdft_mix_step(sdft_ctx* ctx, const double* x_in, const double* x_out, double* x_next);
 
 /* Fermi level by bisection on sum_k w_k sum_n g = N_e; eig [nspin][nkpt][nstates] (device);
  * occ receives g (device), mu/ts written to host scalars. */

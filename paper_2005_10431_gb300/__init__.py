@@ -21,7 +21,7 @@ __all__ = [
     "sdft_set_density", "sdft_get_forces", "sdft_get_scf_log", "sdft_get_pseudocharge", "sdft_get_sad_density",
     "sdft_set_orbitals", "sdft_get_orbitals", "sdft_set_veff", "sdft_apply_h", "sdft_chebyshev_filter",
     "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_subspace_matrices_noalloc", "sdft_subspace_eig", "sdft_chebyshev_filter_multi", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
-    "sdft_lanczos_bounds", "sdft_launch_count", "sdft_get_stencil_variant", "sdft_set_timing", "sdft_get_kernel_stats",
+    "sdft_lanczos_bounds", "sdft_kerker", "sdft_mix_step", "sdft_launch_count", "sdft_get_stencil_variant", "sdft_set_timing", "sdft_get_kernel_stats",
     "sdft_reset_kernel_stats", "pack_block", "unpack_block", "block_shape",
     "SDFT_MLP_NFEAT", "SDFT_MLP_NPARAM", "sdft_mlp_dataset", "sdft_mlp_loss_grad", "sdft_mlp_adam",
     "sdft_mlp_train", "sdft_mlp_forward", "sdft_mlp_predict",
@@ -308,6 +308,18 @@ def sdft_subspace_eig(ctx: Context, is_complex: bool, m, hs, eig, ncol: int):
 def sdft_rotate(ctx: Context, kpt: int, precision: int, y, q, x, ncol: int):
     _check(_lib.lib().sdft_rotate(ctx.handle, kpt, precision, _ptr(y), _ptr(q), _ptr(x), ncol), ctx.handle)
     return x
+
+
+def sdft_kerker(ctx: Context, f, out, nchan: int = 1, k0: float = 0.8, tol: float = 1e-10, max_iter: int = 2000):
+    """out = (-L)(-L + k0^2)^-1 f per channel (device FP64 [nchan][ngrid]); see include/sdft.h."""
+    _check(_lib.lib().sdft_kerker(ctx.handle, _ptr(f), _ptr(out), nchan, k0, tol, max_iter), ctx.handle)
+    return out
+
+
+def sdft_mix_step(ctx: Context, x_in, x_out, x_next):
+    """One step of the context's density mixer (plain or Kerker-preconditioned Pulay); device FP64."""
+    _check(_lib.lib().sdft_mix_step(ctx.handle, _ptr(x_in), _ptr(x_out), _ptr(x_next)), ctx.handle)
+    return x_next
 
 
 def sdft_poisson(ctx: Context, f, phi, tol: float = 1e-10, max_iter: int = 2000) -> int:

@@ -51,7 +51,7 @@ class sdft_options(C.Structure):
         ("pulay_period", C.c_int), ("pulay_restart", C.c_int), ("scf_tol", C.c_double), ("max_scf", C.c_int),
         ("precision", C.c_int), ("final_fp64_pass", C.c_int), ("poisson_tol", C.c_double),
         ("init_guess", C.c_int), ("initial_moment", C.c_double), ("seed", C.c_uint64),
-        ("batch_problems", C.c_int), ("use_graphs", C.c_int),
+        ("batch_problems", C.c_int), ("use_graphs", C.c_int), ("kerker_k0", C.c_double),
     ]
 
 
@@ -115,6 +115,8 @@ SIGNATURES = {
     "sdft_poisson": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int)]),
     "sdft_lda": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t]),
     "sdft_fermi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "sdft_kerker": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int]),
+    "sdft_mix_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sdft_lanczos_bounds": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]),
     "sdft_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),

@@ -344,6 +344,8 @@ sdft_status sdft_create(const sdft_cell* cell, const sdft_grid* grid, const sdft
         SDFT_REQUIRE(o.cheb_degree >= 1 && o.lanczos_steps >= 2, SDFT_ERR_INVALID_ARG, "degree / lanczos steps");
         SDFT_REQUIRE(o.kT > 0 && std::isfinite(o.kT), SDFT_ERR_INVALID_ARG, "kT must be positive");
         SDFT_REQUIRE(o.mix_hist >= 1 && o.mix_hist <= 16, SDFT_ERR_INVALID_ARG, "mix_hist must be in [1, 16]");
+        SDFT_REQUIRE(std::isfinite(o.kerker_k0) && o.kerker_k0 >= 0.0, SDFT_ERR_INVALID_ARG,
+                     "kerker_k0 must be finite and >= 0");
         SDFT_REQUIRE(o.pulay_period >= 1, SDFT_ERR_INVALID_ARG, "pulay_period must be >= 1");
         SDFT_REQUIRE(o.max_scf >= 1, SDFT_ERR_INVALID_ARG, "max_scf must be >= 1");
         c->opt = o;
@@ -602,6 +604,31 @@ sdft_status sdft_poisson(sdft_ctx* c, const double* f, double* phi, double tol, 
         SDFT_CUDA(cudaStreamSynchronize(c->stream));
         if (iters) *iters = it < 0 ? -it : it;
         if (it < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Poisson AAR did not reach the tolerance"};
+    })
+}
+
+sdft_status sdft_kerker(sdft_ctx* c, const double* f, double* out, int nchan, double k0, double tol, int max_iter) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(f && out && f != out && nchan >= 1 && std::isfinite(k0) && k0 > 0 && tol > 0 && max_iter >= 1,
+                     SDFT_ERR_INVALID_ARG, "arguments");
+        for (int ch = 0; ch < nchan; ++ch) {
+            const int it = sdft::kerker_apply(c, f + (long long)ch * c->ng, out + (long long)ch * c->ng, k0, tol,
+                                              max_iter);
+            if (it < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Kerker screened-Poisson solve did not reach tol"};
+        }
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_mix_step(sdft_ctx* c, const double* x_in, const double* x_out, double* x_next) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(x_in && x_out && x_next && x_next != x_in && x_next != x_out, SDFT_ERR_INVALID_ARG, "arguments");
+        const size_t bytes = sizeof(double) * (size_t)c->opt.nspin * (size_t)c->ng;
+        SDFT_CUDA(cudaMemcpyAsync(c->rho_in, x_in, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        SDFT_CUDA(cudaMemcpyAsync(c->rho_out, x_out, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        sdft::pulay_update(c);
+        SDFT_CUDA(cudaMemcpyAsync(x_next, c->rho_in, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
     })
 }
 

@@ -720,7 +720,7 @@ struct LapCoef {
 template <typename T>
 __global__ void __launch_bounds__(256) laplacian_residual_kernel(const T* __restrict__ x, const T* __restrict__ b,
                                                                  T* __restrict__ out, LapCoef K, int n1, int n2,
-                                                                 int n3) {
+                                                                 int n3, T shift) {
     // 32-bit indices: the grid has < 2^31 points
     const int plane = n1 * n2;
     const int ng = plane * n3;
@@ -745,12 +745,12 @@ __global__ void __launch_bounds__(256) laplacian_residual_kernel(const T* __rest
         acc += (T)K.c[1][r] * (x[col + jp * n1] + x[col + jm * n1]);
         acc += (T)K.c[2][r] * (x[pl + kp * plane] + x[pl + km * plane]);
     }
-    // -L x = 2 * (-1/2 L x): out = b + L x = b - 2 acc
-    out[g] = b[g] - (T)2 * acc;
+    // -L x = 2 * (-1/2 L x): out = b + L x - shift x = b - 2 acc - shift x  (residual of (-L + shift) x = b)
+    out[g] = b[g] - (T)2 * acc - shift * x[g];
 }
 
 template <typename T>
-void laplacian_residual(sdft_ctx* c, const T* x, const T* b, T* out) {
+void laplacian_residual(sdft_ctx* c, const T* x, const T* b, T* out, T shift = T(0)) {
     LapCoef K;
     for (int r = 0; r <= FD_RADIUS; ++r) {
         K.c[0][r] = c->coef.cx[r];
@@ -759,7 +759,7 @@ void laplacian_residual(sdft_ctx* c, const T* x, const T* b, T* out) {
     }
     K.c0 = c->coef.c0;
     laplacian_residual_kernel<T><<<(unsigned)((c->ng + 255) / 256), 256, 0, c->stream>>>(x, b, out, K, c->n[0],
-                                                                                        c->n[1], c->n[2]);
+                                                                                        c->n[1], c->n[2], shift);
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);
 }
@@ -1288,6 +1288,114 @@ void fermi_device(sdft_ctx* c, const double* eig, double* occ, double* out) {
     count_launch(c);
 }
 
+// ---------------------------------------------------------------------------------------
+// Kerker preconditioner of the mixing (paper Sec. 2.1: periodic Pulay with a real-space
+// preconditioner of Kerker type): P f = (-L_h)(-L_h + k0^2)^-1 f = f - k0^2 y, (-L_h + k0^2) y = f.
+// The screened operator is positive definite, so y comes from the same AAR iteration as the
+// Poisson solve (Jacobi-preconditioned Richardson steps, Anderson extrapolation every p-th step),
+// with the diagonal shift k0^2 in the residual and in the Jacobi factor; no gauge is involved.
+// ---------------------------------------------------------------------------------------
+namespace {
+constexpr int KERKER_M = 7, KERKER_P = 6;
+constexpr double KERKER_TOL = 1e-10;    // relative residual of the screened solve inside the SCF
+
+// x_k ← x_k - sum_j gamma_j X_j and f ← beta (f - sum_j gamma_j F_j): the optimal residual form of a
+// Pulay step, whose linear part is then preconditioned
+__global__ void pulay_residual_kernel(double* __restrict__ x, double* __restrict__ f, const double* __restrict__ X,
+                                      const double* __restrict__ F, const int* __restrict__ slots,
+                                      const double* __restrict__ gamma, int m, double beta, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double xv = x[i], fv = f[i];
+        for (int j = 0; j < m; ++j) {
+            const long long o = (long long)slots[j] * n + i;
+            xv -= gamma[j] * X[o];
+            fv -= gamma[j] * F[o];
+        }
+        x[i] = xv;
+        f[i] = beta * fv;
+    }
+}
+}  // namespace
+
+static double* kerker_workspace(sdft_ctx* c) {
+    // rhs copy, solution, AAR residual, previous iterate and residual, X[m], F[m]
+    if (!c->kerker_ws) c->kerker_ws = (double*)ctx_alloc(c, sizeof(double) * (size_t)(5 + 2 * KERKER_M) * c->ng);
+    return c->kerker_ws;
+}
+
+int kerker_apply(sdft_ctx* c, const double* f, double* out, double k0, double tol, int max_iter) {
+    const long long n = c->ng;
+    SDFT_REQUIRE(k0 > 0.0 && tol > 0.0 && max_iter >= 1, SDFT_ERR_INVALID_ARG, "Kerker: k0 > 0, tol > 0 required");
+    double* ws = kerker_workspace(c);
+    double* y = ws + 1 * n;
+    double* r = ws + 2 * n;
+    double* xprev = ws + 3 * n;
+    double* fprev = ws + 4 * n;
+    double* Xs = ws + 5 * n;
+    double* Fs = Xs + (long long)KERKER_M * n;
+    double* gam = c->scal + 64;
+    int* slots = (int*)(c->scal + 96);
+    double* ffv = c->scal + 128;
+    double* part = c->scal + 4096;
+    const double k2 = k0 * k0;
+    const double cj = 1.0 / (2.0 * c->coef.c0 + k2);   // Jacobi: diag(-L_h + k0^2)
+    const double omega = 0.6, beta = 0.6;
+    double bnorm2;
+    {
+        const double* A[1] = {f};
+        dots_host(c, 1, A, A, n, &bnorm2);
+    }
+    SDFT_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, c->stream));
+    int it = 0;
+    if (bnorm2 > 0.0) {
+        int count = 0, head = 0;
+        int hslots[16];
+        bool done = false;
+        for (it = 0; it < max_iter; ++it) {
+            laplacian_residual<double>(c, y, f, r, k2);
+            anderson_push_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(y, r, cj, xprev, fprev,
+                                                                            Xs + (long long)head * n,
+                                                                            Fs + (long long)head * n, it > 0, n);
+            count_launch(c);
+            if (it > 0) {
+                head = (head + 1) % KERKER_M;
+                count = std::min(count + 1, KERKER_M);
+            }
+            if (((it + 1) % KERKER_P == 0) && count > 0) {
+                for (int j = 0; j < count; ++j) hslots[j] = ((head - count + j) % KERKER_M + KERKER_M) % KERKER_M;
+                std::memcpy(c->hscal + 512, hslots, sizeof(int) * 16);
+                SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 512, sizeof(int) * count, cudaMemcpyHostToDevice, c->stream));
+                anderson_gram_kernel<double><<<64, RB, 0, c->stream>>>(Fs, slots, count, r, cj, n, part);
+                anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part, 64, count, gam, ffv);
+                anderson_update_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(y, r, cj, beta, Xs, Fs, slots, gam,
+                                                                                  count, n);
+                SDFT_CUDA(cudaGetLastError());
+                count_launch(c, 3);
+                SDFT_CUDA(cudaMemcpyAsync(c->hscal, ffv, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+                SDFT_CUDA(cudaStreamSynchronize(c->stream));
+                const double rn2 = c->hscal[0] / (cj * cj);
+                if (!std::isfinite(rn2)) throw Error{SDFT_ERR_NONFINITE, "Kerker solve residual is not finite"};
+                if (rn2 <= tol * tol * bnorm2) {
+                    ++it;
+                    done = true;
+                    break;
+                }
+            } else {
+                axpby_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(y, r, omega * cj, 1.0, n);
+                SDFT_CUDA(cudaGetLastError());
+                count_launch(c);
+            }
+        }
+        if (!done) return -it;
+    }
+    // out = f - k0^2 y
+    SDFT_CUDA(cudaMemcpyAsync(out, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    axpby_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(out, y, -k2, 1.0, n);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+    return std::max(it, 1);
+}
+
 // Pulay mixing on rho_in (paper Sec. 2.1; Banerjee et al. 2016, Pratapa & Suryanarayana 2015):
 // f = rho_out - rho_in; linear step rho += beta f, or Pulay every period-th iteration.
 void pulay_update(sdft_ctx* c) {
@@ -1308,6 +1416,42 @@ void pulay_update(sdft_ctx* c) {
         c->mix_count = std::min(c->mix_count + 1, m);
     }
     const bool pulay = c->mix_k > 0 && c->mix_count > 0 && ((c->mix_k + 1) % c->opt.pulay_period == 0);
+    if (c->opt.kerker_k0 > 0.0) {
+        // Kerker-preconditioned form: x <- x - X gamma + P(beta (f - F gamma)), P channel by channel
+        if (pulay) {
+            int hslots[16];
+            const int cnt = c->mix_count;
+            for (int j = 0; j < cnt; ++j) hslots[j] = ((c->mix_head - cnt + j) % m + m) % m;
+            int* slots = (int*)(c->scal + 160);
+            double* gam = c->scal + 192;
+            double* ffv = c->scal + 224;
+            double* part = c->scal + 4096;
+            std::memcpy(c->hscal + 640, hslots, sizeof(int) * 16);
+            SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 640, sizeof(int) * cnt, cudaMemcpyHostToDevice, c->stream));
+            const int nblk = 32;
+            anderson_gram_kernel<double><<<nblk, RB, 0, c->stream>>>(c->mix_df, slots, cnt, f, 1.0, n, part);
+            anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part, nblk, cnt, gam, ffv);
+            pulay_residual_kernel<<<nblocks(n), 256, 0, c->stream>>>(c->rho_in, f, c->mix_dx, c->mix_df, slots, gam, cnt,
+                                                                     c->opt.mix_beta, n);
+            count_launch(c, 3);
+            if (c->opt.pulay_restart) c->mix_count = 0;
+        } else {
+            axpby_kernel<double><<<nblocks(n), 256, 0, c->stream>>>(f, f, 0.0, c->opt.mix_beta, n);
+            count_launch(c);
+        }
+        SDFT_CUDA(cudaGetLastError());
+        double* pf = c->work64 + 2 * c->ng;   // P of one channel
+        for (int sp = 0; sp < c->opt.nspin; ++sp) {
+            const int it = kerker_apply(c, f + (long long)sp * c->ng, pf, c->opt.kerker_k0, KERKER_TOL, 4000);
+            if (it < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Kerker screened-Poisson solve did not converge"};
+            axpby_kernel<double><<<nblocks(c->ng), 256, 0, c->stream>>>(c->rho_in + (long long)sp * c->ng, pf, 1.0, 1.0,
+                                                                        c->ng);
+            count_launch(c);
+        }
+        SDFT_CUDA(cudaGetLastError());
+        c->mix_k += 1;
+        return;
+    }
     if (pulay) {
         int hslots[16];
         const int cnt = c->mix_count;

@@ -208,6 +208,7 @@ struct sdft_ctx {
     double* mix_xprev = nullptr;
     double* mix_fprev = nullptr;
     int mix_k = 0, mix_count = 0, mix_head = 0;
+    double* kerker_ws = nullptr;  // screened-Poisson AAR workspace of the Kerker preconditioner (first use)
     bool user_density = false;
     void* mlp_scratch = nullptr;  // learned guess: features [ng][32] bf16 + output [ng] (allocated on first use)
 
@@ -315,6 +316,9 @@ void fermi_device(sdft_ctx* c, const double* eig, double* occ, double* mu_ts_dev
 void density_accumulate(sdft_ctx* c, int precision, bool cplx, const void* X, const double* occ,
                         int ncol, double weight, double* rho);
 void pulay_update(sdft_ctx* c);
+// Kerker preconditioner out = (-L)(-L + k0^2)^-1 f of one grid vector by a screened AAR solve to relative
+// residual tol; returns the iteration count (negative: not converged)
+int kerker_apply(sdft_ctx* c, const double* f, double* out, double k0, double tol, int max_iter);
 void forces_compute(sdft_ctx* c);
 
 // ---- dense.cu ------------------------------------------------------------------------
