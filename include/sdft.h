@@ -55,6 +55,7 @@ typedef int sdft_status;
 
 enum { SDFT_FP64 = 0, SDFT_MIXED = 1 };
 enum { SDFT_GUESS_SAD = 0, SDFT_GUESS_USER = 1 };
+enum { SDFT_XC_LDA_PZ = 0, SDFT_XC_GGA_PBE = 1 };
 
 typedef struct sdft_ctx sdft_ctx;
 
@@ -117,6 +118,8 @@ typedef struct {
                                   periodic Pulay) with screening wavevector k0 (1/bohr): the linear part of
                                   every update is P(beta r), P = (-L_h)(-L_h + k0^2)^-1 applied channel by
                                   channel through a screened-Poisson AAR solve; 0: plain Pulay */
+    int xc;                    /* exchange-correlation: SDFT_XC_LDA_PZ (Perdew-Zunger LDA, paper Sec. 3) or
+                                  SDFT_XC_GGA_PBE (PBE GGA, paper Sec. 2.2; nspin = 1 only) */
 } sdft_options;
 
 /* Per-iteration record of the SCF (paper Sec. 2.1 ".out" progress). */
@@ -285,7 +288,11 @@ sdft_status sdft_rotate(sdft_ctx* ctx, int kpt, int precision, const void* y, co
 sdft_status sdft_poisson(sdft_ctx* ctx, const double* f, double* phi, double tol, int max_iter,
                          int* iters);
 
-/* Perdew-Zunger LDA (paper Sec. 3): rho [nspin][n] -> eps_xc [n], v_xc [nspin][n]; device FP64. */
+/* Exchange-correlation of the context's functional (opt.xc): rho [nspin][n] -> eps_xc [n] (per electron),
+ * v_xc [nspin][n]; device FP64.  LDA: Perdew-Zunger (paper Sec. 3), pointwise.  GGA: PBE (paper Sec. 2.2),
+ * nspin = 1 and n = ngrid: the gradient is the order-12 centred first-derivative stencil of the grid
+ * (periodic), sigma = |D rho|^2, and v_xc = f_rho - 2 sum_d D_d (f_sigma D_d rho) is the exact derivative of
+ * the discrete energy E_xc = dV sum rho eps_xc.  The density is floored at 1e-14 inside. */
 sdft_status sdft_lda(sdft_ctx* ctx, int nspin, const double* rho, double* exc, double* vxc,
                      size_t n);
 

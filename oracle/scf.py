@@ -19,7 +19,7 @@ import time
 import numpy as np
 
 import workloads
-from . import chefsi, ham, model, xc
+from . import chefsi, gga, ham, model, xc
 
 
 class PulayMixer:
@@ -92,7 +92,12 @@ class Problem:
         """V_eff^s = phi + V_xc^s (Sec. 2.1); returns (veff (nspin, ngrid), phi, exc per electron)."""
         rho_tot = rho.sum(axis=0)
         phi = ham.poisson_exact(self.cell, rho_tot + self.b)
-        if self.cell.nspin == 1:
+        if getattr(self.cell, "xc", "lda_pz") == "gga_pbe":
+            if self.cell.nspin != 1:
+                raise ValueError("the PBE oracle is spin-unpolarized")
+            exc, vxc = gga.pbe_unpolarized(self.cell, rho_tot)
+            vxc = vxc[None, :]
+        elif self.cell.nspin == 1:
             exc, vxc = xc.lda_pz_unpolarized(rho_tot)
             vxc = vxc[None, :]
         else:

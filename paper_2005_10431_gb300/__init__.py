@@ -12,7 +12,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (SDFT_FP64, SDFT_MIXED, SDFT_GUESS_SAD, SDFT_GUESS_USER, sdft_options,  # noqa: F401
+from ._lib import (SDFT_FP64, SDFT_MIXED, SDFT_GUESS_SAD, SDFT_GUESS_USER, SDFT_XC_LDA_PZ, SDFT_XC_GGA_PBE, sdft_options,  # noqa: F401
                    sdft_iter_record, sdft_result, SDFT_MLP_NFEAT, SDFT_MLP_NPARAM)
 
 __all__ = [

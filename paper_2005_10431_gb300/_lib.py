@@ -22,6 +22,8 @@ SDFT_FP64 = 0
 SDFT_MIXED = 1
 SDFT_GUESS_SAD = 0
 SDFT_GUESS_USER = 1
+SDFT_XC_LDA_PZ = 0
+SDFT_XC_GGA_PBE = 1
 
 ERROR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "CHOLESKY",
                -6: "DEVICE_TIMEOUT", -7: "NONFINITE"}
@@ -52,6 +54,7 @@ class sdft_options(C.Structure):
         ("precision", C.c_int), ("final_fp64_pass", C.c_int), ("poisson_tol", C.c_double),
         ("init_guess", C.c_int), ("initial_moment", C.c_double), ("seed", C.c_uint64),
         ("batch_problems", C.c_int), ("use_graphs", C.c_int), ("kerker_k0", C.c_double),
+        ("xc", C.c_int),
     ]
 
 

@@ -346,6 +346,8 @@ sdft_status sdft_create(const sdft_cell* cell, const sdft_grid* grid, const sdft
         SDFT_REQUIRE(o.mix_hist >= 1 && o.mix_hist <= 16, SDFT_ERR_INVALID_ARG, "mix_hist must be in [1, 16]");
         SDFT_REQUIRE(std::isfinite(o.kerker_k0) && o.kerker_k0 >= 0.0, SDFT_ERR_INVALID_ARG,
                      "kerker_k0 must be finite and >= 0");
+        SDFT_REQUIRE(o.xc == SDFT_XC_LDA_PZ || (o.xc == SDFT_XC_GGA_PBE && o.nspin == 1), SDFT_ERR_INVALID_ARG,
+                     "xc must be SDFT_XC_LDA_PZ, or SDFT_XC_GGA_PBE with nspin = 1");
         SDFT_REQUIRE(o.pulay_period >= 1, SDFT_ERR_INVALID_ARG, "pulay_period must be >= 1");
         SDFT_REQUIRE(o.max_scf >= 1, SDFT_ERR_INVALID_ARG, "max_scf must be >= 1");
         c->opt = o;

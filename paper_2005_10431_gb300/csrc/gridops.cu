@@ -683,7 +683,160 @@ void build_pseudocharge_and_sad(sdft_ctx* c) {
     count_launch(c);
 }
 
+// ---------------------------------------------------------------------------------------
+// PBE GGA, spin-unpolarized (paper Sec. 2.2 functionalities; Perdew, Burke & Ernzerhof 1996 with the
+// Perdew-Wang 1992 correlation of the uniform gas).  On the grid: g_d = D_d rho with the order-12
+// centred first-derivative stencil (periodic), sigma = sum_d g_d^2, f(rho, sigma) = rho eps_xc, and
+// v_xc = f_rho - 2 sum_d D_d (f_sigma g_d), the exact derivative of E_xc = dV sum_g f (D_d^T = -D_d).
+// ---------------------------------------------------------------------------------------
+namespace {
+struct D1Coef {
+    double c[3][FD_RADIUS + 1];   // c_k / h_d, k = 1..6: (D_d u)(x) = sum_k c_k (u(x + k e_d) - u(x - k e_d))
+};
+
+// out_d = D_d u for the three axes (in0 == in1 == in2 == u), or out0 -= sum_d D_d in_d (accumulate)
+template <bool DIV>
+__global__ void __launch_bounds__(256) d1_kernel(const double* __restrict__ in0, const double* __restrict__ in1,
+                                                 const double* __restrict__ in2, double* __restrict__ out0,
+                                                 double* __restrict__ out1, double* __restrict__ out2, D1Coef K,
+                                                 int n1, int n2, int n3) {
+    const int plane = n1 * n2;
+    const int ng = plane * n3;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    const int k = g / plane;
+    const int rem = g - k * plane;
+    const int j = rem / n1;
+    const int i = rem - j * n1;
+    const int row = g - i, col = g - j * n1, pl = g - k * plane;
+    double dx = 0.0, dy = 0.0, dz = 0.0;
+#pragma unroll
+    for (int r = 1; r <= FD_RADIUS; ++r) {
+        int ip = i + r, im = i - r, jp = j + r, jm = j - r, kp = k + r, km = k - r;
+        ip -= ip >= n1 ? n1 : 0;
+        im += im < 0 ? n1 : 0;
+        jp -= jp >= n2 ? n2 : 0;
+        jm += jm < 0 ? n2 : 0;
+        kp -= kp >= n3 ? n3 : 0;
+        km += km < 0 ? n3 : 0;
+        dx += K.c[0][r] * (in0[row + ip] - in0[row + im]);
+        dy += K.c[1][r] * (in1[col + jp * n1] - in1[col + jm * n1]);
+        dz += K.c[2][r] * (in2[pl + kp * plane] - in2[pl + km * plane]);
+    }
+    if (DIV) {
+        out0[g] -= dx + dy + dz;
+    } else {
+        out0[g] = dx;
+        out1[g] = dy;
+        out2[g] = dz;
+    }
+}
+
+constexpr double PBE_KAPPA = 0.804;
+constexpr double PBE_BETA = 0.06672455060314922;
+constexpr double PW92_A = 0.031091, PW92_A1 = 0.21370, PW92_B1 = 7.5957, PW92_B2 = 3.5876, PW92_B3 = 1.6382,
+                 PW92_B4 = 0.49294;
+
+// eps_xc (per electron), f_rho and f_sigma of PBE at one point, analytic derivatives
+__device__ void pbe_eval(double rho, double sigma, double& eps, double& frho, double& fsig) {
+    const double pi = 3.14159265358979323846;
+    const double mu = PBE_BETA * pi * pi / 3.0;
+    const double gam = (1.0 - log(2.0)) / (pi * pi);
+    const double r = fmax(rho, 1e-14);
+    const double kf = cbrt(3.0 * pi * pi * r);
+    const double exu = -3.0 * kf / (4.0 * pi);
+    // exchange: f_x = r exu F_x(s2), s2 = sigma / (4 kf^2 r^2) ~ sigma r^(-8/3)
+    const double s2den = 4.0 * kf * kf * r * r;
+    const double s2 = sigma / s2den;
+    const double den = PBE_KAPPA + mu * s2;
+    const double Fx = 1.0 + PBE_KAPPA - PBE_KAPPA * PBE_KAPPA / den;
+    const double dFx = mu * PBE_KAPPA * PBE_KAPPA / (den * den);   // dF_x / ds2
+    const double fx = r * exu * Fx;
+    const double fx_r = (4.0 / 3.0) * exu * Fx - (8.0 / 3.0) * exu * dFx * s2;
+    const double fx_s = r * exu * dFx / s2den;
+    // PW92 correlation of the uniform gas, eps_c(rs), rs = (3 / (4 pi r))^(1/3)
+    const double rs = cbrt(3.0 / (4.0 * pi * r));
+    const double sq = sqrt(rs);
+    const double Q = 2.0 * PW92_A * (PW92_B1 * sq + PW92_B2 * rs + PW92_B3 * rs * sq + PW92_B4 * rs * rs);
+    const double dQ = 2.0 * PW92_A * (0.5 * PW92_B1 / sq + PW92_B2 + 1.5 * PW92_B3 * sq + 2.0 * PW92_B4 * rs);
+    const double Lq = log1p(1.0 / Q);
+    const double ec = -2.0 * PW92_A * (1.0 + PW92_A1 * rs) * Lq;
+    const double dec_drs = -2.0 * PW92_A * PW92_A1 * Lq + 2.0 * PW92_A * (1.0 + PW92_A1 * rs) * dQ / (Q * (1.0 + Q));
+    const double dec_dr = -dec_drs * rs / (3.0 * r);
+    // gradient correction H(ec, t2), t2 = sigma / (4 ks^2 r^2) ~ sigma r^(-7/3), ks^2 = 4 kf / pi
+    const double t2den = 16.0 * kf * r * r / pi;
+    const double t2 = sigma / t2den;
+    const double E = exp(-ec / gam);
+    const double A = (PBE_BETA / gam) / (E - 1.0);
+    const double dA_dec = (PBE_BETA / (gam * gam)) * E / ((E - 1.0) * (E - 1.0));
+    const double y = A * t2;
+    const double Dn = 1.0 + y + y * y;
+    const double Z = (PBE_BETA / gam) * t2 * (1.0 + y) / Dn;
+    const double H = gam * log1p(Z);
+    const double dH_dt2 = PBE_BETA * (1.0 + 2.0 * y) / ((1.0 + Z) * Dn * Dn);
+    const double dH_dA = -PBE_BETA * t2 * t2 * y * (2.0 + y) / ((1.0 + Z) * Dn * Dn);
+    const double fc = r * (ec + H);
+    const double fc_r = ec + H + r * dec_dr * (1.0 + dH_dA * dA_dec) - (7.0 / 3.0) * dH_dt2 * t2;
+    const double fc_s = r * dH_dt2 / t2den;
+    eps = (fx + fc) / r;
+    frho = fx_r + fc_r;
+    fsig = fx_s + fc_s;
+}
+
+// exc = eps_xc, vxc = f_rho, w_d = 2 f_sigma g_d  (the divergence kernel then subtracts sum_d D_d w_d)
+__global__ void pbe_point_kernel(const double* __restrict__ rho, const double* __restrict__ g0,
+                                 const double* __restrict__ g1, const double* __restrict__ g2,
+                                 double* __restrict__ exc, double* __restrict__ vxc, double* __restrict__ w0,
+                                 double* __restrict__ w1, double* __restrict__ w2, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double a = g0[i], b = g1[i], cc = g2[i];
+        double eps, fr, fs;
+        pbe_eval(rho[i], a * a + b * b + cc * cc, eps, fr, fs);
+        exc[i] = eps;
+        vxc[i] = fr;
+        w0[i] = 2.0 * fs * a;
+        w1[i] = 2.0 * fs * b;
+        w2[i] = 2.0 * fs * cc;
+    }
+}
+}  // namespace
+
+static void gga_pbe_device(sdft_ctx* c, const double* rho, double* exc, double* vxc) {
+    const long long n = c->ng;
+    if (!c->gga_ws) c->gga_ws = (double*)ctx_alloc(c, sizeof(double) * 6 * (size_t)n);
+    double* g = c->gga_ws;
+    double* w = c->gga_ws + 3 * n;
+    // first-derivative weights c_k = (-1)^(k+1) (p!)^2 / (k (p-k)! (p+k)!), p = 6
+    D1Coef K;
+    {
+        auto fact = [](int m) {
+            double f = 1.0;
+            for (int q = 2; q <= m; ++q) f *= q;
+            return f;
+        };
+        const int p = FD_RADIUS;
+        for (int d = 0; d < 3; ++d) {
+            K.c[d][0] = 0.0;
+            for (int k = 1; k <= p; ++k)
+                K.c[d][k] = ((k % 2) ? 1.0 : -1.0) * fact(p) * fact(p) / (k * fact(p - k) * fact(p + k)) / c->h[d];
+        }
+    }
+    const unsigned nbk = (unsigned)((n + 255) / 256);
+    d1_kernel<false><<<nbk, 256, 0, c->stream>>>(rho, rho, rho, g, g + n, g + 2 * n, K, c->n[0], c->n[1], c->n[2]);
+    pbe_point_kernel<<<nblocks(n), 256, 0, c->stream>>>(rho, g, g + n, g + 2 * n, exc, vxc, w, w + n, w + 2 * n, n);
+    d1_kernel<true><<<nbk, 256, 0, c->stream>>>(w, w + n, w + 2 * n, vxc, nullptr, nullptr, K, c->n[0], c->n[1],
+                                                 c->n[2]);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c, 3);
+}
+
 void lda_device(sdft_ctx* c, int nspin, const double* rho, double* exc, double* vxc, size_t n) {
+    if (c->opt.xc == SDFT_XC_GGA_PBE) {
+        SDFT_REQUIRE(nspin == 1 && (long long)n == c->ng, SDFT_ERR_INVALID_ARG,
+                     "PBE: spin-unpolarized densities on the context's grid only");
+        gga_pbe_device(c, rho, exc, vxc);
+        return;
+    }
     lda_kernel<<<nblocks((long long)n), 256, 0, c->stream>>>(nspin, rho, exc, vxc, (long long)n);
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);

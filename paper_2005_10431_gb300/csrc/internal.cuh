@@ -209,6 +209,7 @@ struct sdft_ctx {
     double* mix_fprev = nullptr;
     int mix_k = 0, mix_count = 0, mix_head = 0;
     double* kerker_ws = nullptr;  // screened-Poisson AAR workspace of the Kerker preconditioner (first use)
+    double* gga_ws = nullptr;     // PBE: density gradient and f_sigma-weighted gradient, 6 ng (first use)
     bool user_density = false;
     void* mlp_scratch = nullptr;  // learned guess: features [ng][32] bf16 + output [ng] (allocated on first use)
 

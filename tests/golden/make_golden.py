@@ -29,6 +29,14 @@ def qmd8_72():
     return c
 
 
+def two_atom_pbe():
+    """The two-atom cell with the PBE GGA functional (spin-unpolarized)."""
+    c = workloads.two_atom_cell()
+    c.xc = "gga_pbe"
+    c.name = "two_atom_24_pbe"
+    return c
+
+
 # Solver choices (buffer vectors, Chebyshev degree, Kerker-preconditioned mixing) only change how fast
 # the oracle reaches the fixed point, not the fixed point itself (oracle/scf.py).  The 64-atom cell
 # needs them: with 154 states its partially occupied top states sit next to the filter cutoff, and
@@ -39,6 +47,7 @@ CELLS = {
                                                     kerker_k0=0.8)),
     "kspin_20": (workloads.kspin_small_cell, dict(tol=1e-8, max_iter=300, final_tol=None)),
     "qmd8_72": (qmd8_72, dict(tol=1e-10, max_iter=120, final_tol=1e-9, nbuffer=8, kerker_k0=0.8)),
+    "two_atom_24_pbe": (two_atom_pbe, dict(tol=1e-10, max_iter=300, final_tol=1e-10)),
 }
 
 
@@ -49,7 +58,7 @@ def main(names):
         t0 = time.time()
         r = scf.scf(cell, with_forces=True, verbose=True, **kw)
         out = dict(
-            cell=name,
+            cell=name, xc=getattr(cell, "xc", "lda_pz"),
             generator="tests/golden/make_golden.py (oracle.scf.scf, FP64 CPU)",
             scf_options=dict(dict(mix_beta=0.3, mix_hist=7, pulay_period=1, first_passes=4, lanczos_steps=20),
                              **kw),

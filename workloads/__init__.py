@@ -87,6 +87,7 @@ class Cell:
     kw: np.ndarray = None       # (nk,) weights summing to 1
     scf_tol: float = 1e-6
     seed: int = 0
+    xc: str = "lda_pz"          # exchange-correlation functional: "lda_pz" or "gga_pbe" (unpolarized)
 
     @property
     def natom(self) -> int:
