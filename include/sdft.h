@@ -185,6 +185,23 @@ sdft_status sdft_batch_scf(sdft_ctx* const* ctxs, int n, sdft_result* out);
  * density guess to the SAD (or last user) density, so that sdft_scf can be repeated. */
 sdft_status sdft_reset(sdft_ctx* ctx);
 
+/* Move the atoms (pos: natom*3 bohr, host; same species and count) and prepare the next sdft_scf (paper
+ * Sec. 2.1: in quantum molecular dynamics the density guess of later steps is extrapolated from earlier
+ * ones, after D. Alfe, Comput. Phys. Commun. 118 (1999) 31).  The pseudocharge, SAD density, KB tables
+ * and overlap energies are rebuilt for the new positions and the mixing history is cleared.
+ *   guess = 0: start from the SAD density and seeded orbitals, as a new context would.
+ *   guess = 1: start from the extrapolated density
+ *       rho = rho_SAD(R) + (1 + alpha) D_0 + (beta - alpha) D_1 - beta D_2,
+ *     D_i = rho_out - rho_SAD(R_i) of this context's i-th most recent SCF (positions R_i), where alpha,
+ *     beta fit R - R_0 ~ alpha (R_0 - R_1) + beta (R_1 - R_2) in the least-squares sense (minimum-image
+ *     differences; with two past SCFs beta = 0, with one alpha = beta = 0, with none guess 0 is used),
+ *     clamped at 0 and renormalised to N_e; the orbitals and filter bounds of the last SCF are kept
+ *     (the upper bound refreshed by Lanczos) and the first SCF iteration filters once.
+ * coef (host, 2 doubles, may be NULL) receives alpha, beta.  Synchronises the stream. */
+sdft_status sdft_move_atoms(sdft_ctx* ctx, const double* pos, int guess, double* coef);
+/* The density the next sdft_scf starts from, [spin][ngrid] (host or device). */
+sdft_status sdft_get_input_density(sdft_ctx* ctx, double* dst, size_t n, int on_device);
+
 /* Eigenvalues [spin][k][state], n >= nspin*nkpt*nstates. Host. */
 sdft_status sdft_get_eigenvalues(sdft_ctx* ctx, double* host, size_t n);
 /* Occupations g (same layout), host. */

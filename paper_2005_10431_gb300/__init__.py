@@ -21,7 +21,7 @@ __all__ = [
     "sdft_set_density", "sdft_get_forces", "sdft_get_scf_log", "sdft_get_pseudocharge", "sdft_get_sad_density",
     "sdft_set_orbitals", "sdft_get_orbitals", "sdft_set_veff", "sdft_apply_h", "sdft_chebyshev_filter",
     "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_subspace_matrices_noalloc", "sdft_subspace_eig", "sdft_chebyshev_filter_multi", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
-    "sdft_lanczos_bounds", "sdft_kerker", "sdft_mix_step", "sdft_launch_count", "sdft_get_stencil_variant", "sdft_set_timing", "sdft_get_kernel_stats",
+    "sdft_lanczos_bounds", "sdft_kerker", "sdft_mix_step", "sdft_move_atoms", "sdft_get_input_density", "sdft_launch_count", "sdft_get_stencil_variant", "sdft_set_timing", "sdft_get_kernel_stats",
     "sdft_reset_kernel_stats", "pack_block", "unpack_block", "block_shape",
     "SDFT_MLP_NFEAT", "SDFT_MLP_NPARAM", "sdft_mlp_dataset", "sdft_mlp_loss_grad", "sdft_mlp_adam",
     "sdft_mlp_train", "sdft_mlp_forward", "sdft_mlp_predict",
@@ -320,6 +320,22 @@ def sdft_mix_step(ctx: Context, x_in, x_out, x_next):
     """One step of the context's density mixer (plain or Kerker-preconditioned Pulay); device FP64."""
     _check(_lib.lib().sdft_mix_step(ctx.handle, _ptr(x_in), _ptr(x_out), _ptr(x_next)), ctx.handle)
     return x_next
+
+
+def sdft_move_atoms(ctx: Context, pos, guess: int = 1):
+    """Move the atoms (natom x 3 bohr) and prepare the next SCF (0: SAD + seeded orbitals, 1: extrapolated
+    density + kept orbitals); returns the extrapolation coefficients (alpha, beta)."""
+    p = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1))
+    coef = np.zeros(2)
+    _check(_lib.lib().sdft_move_atoms(ctx.handle, p.ctypes.data, guess, coef.ctypes.data), ctx.handle)
+    return float(coef[0]), float(coef[1])
+
+
+def sdft_get_input_density(ctx: Context) -> np.ndarray:
+    """The density [nspin][ngrid] the next sdft_scf starts from (host copy)."""
+    out = np.empty((ctx.nspin, ctx.ngrid))
+    _check(_lib.lib().sdft_get_input_density(ctx.handle, out.ctypes.data, out.size, 0), ctx.handle)
+    return out
 
 
 def sdft_poisson(ctx: Context, f, phi, tol: float = 1e-10, max_iter: int = 2000) -> int:

@@ -120,6 +120,8 @@ SIGNATURES = {
     "sdft_fermi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "sdft_kerker": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int]),
     "sdft_mix_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sdft_move_atoms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "sdft_get_input_density": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]),
     "sdft_lanczos_bounds": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]),
     "sdft_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),

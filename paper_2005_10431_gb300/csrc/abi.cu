@@ -26,6 +26,19 @@ void* ctx_alloc(sdft_ctx* c, size_t bytes) {
     return p;
 }
 
+void ctx_release(sdft_ctx* c, void* p) {
+    if (!p) return;
+    auto it = std::find(c->owned.begin(), c->owned.end(), p);
+    if (it == c->owned.end()) return;
+    c->owned.erase(it);
+    if (c->release) {
+        c->release(p, c->alloc_user);
+    } else {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(p);
+    }
+}
+
 void ctx_free_all(sdft_ctx* c) {
     if (c->stream || true) cudaStreamSynchronize(c->stream);
     for (void* p : c->owned) {
@@ -109,6 +122,8 @@ bool finite_all(const double* p, size_t n) {
     return true;
 }
 
+}  // namespace
+
 void host_energy_constants(sdft_ctx* c) {
     // E_self = sum Z^2 / (2 sqrt(pi) r_loc); E_sc = 1/2 sum' Z Z' erfc(d/s)/d, s = sqrt(2(r^2 + r'^2))
     c->E_self = 0.0;
@@ -146,6 +161,9 @@ void host_energy_constants(sdft_ctx* c) {
         }
     }
 }
+
+namespace {
+
 
 void build_context(sdft_ctx* c) {
     const sdft_options& o = c->opt;
@@ -487,6 +505,29 @@ sdft_status sdft_set_density(sdft_ctx* c, const double* src, size_t n, int on_de
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
         SDFT_CUDA(cudaMemcpyAsync(c->rho_in, c->rho_user, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
         c->user_density = true;
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_move_atoms(sdft_ctx* c, const double* pos, int guess, double* coef) {
+    SDFT_TRY(c, {
+        SDFT_REQUIRE(pos != nullptr && (guess == 0 || guess == 1), SDFT_ERR_INVALID_ARG, "arguments");
+        SDFT_REQUIRE(sdft::finite_all(pos, 3 * (size_t)c->natom), SDFT_ERR_NONFINITE, "positions contain NaN/Inf");
+        sdft::move_atoms(c, pos, guess);
+        if (coef) {
+            coef[0] = guess ? c->last_alfe[0] : 0.0;
+            coef[1] = guess ? c->last_alfe[1] : 0.0;
+        }
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    })
+}
+
+sdft_status sdft_get_input_density(sdft_ctx* c, double* dst, size_t n, int on_device) {
+    SDFT_TRY(c, {
+        const size_t need = (size_t)c->opt.nspin * c->ng;
+        SDFT_REQUIRE(dst != nullptr && n >= need, SDFT_ERR_INVALID_ARG, "buffer shorter than nspin*ngrid");
+        SDFT_CUDA(cudaMemcpyAsync(dst, c->rho_in, sizeof(double) * need,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
         SDFT_CUDA(cudaStreamSynchronize(c->stream));
     })
 }

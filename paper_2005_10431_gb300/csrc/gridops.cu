@@ -681,6 +681,7 @@ void build_pseudocharge_and_sad(sdft_ctx* c) {
     axpby_kernel<double><<<nblocks(c->ng), 256, 0, c->stream>>>(c->rho_sad, c->rho_sad, 0.0, scale, c->ng);
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);
+    ctx_release(c, dat);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -210,6 +210,12 @@ struct sdft_ctx {
     int mix_k = 0, mix_count = 0, mix_head = 0;
     double* kerker_ws = nullptr;  // screened-Poisson AAR workspace of the Kerker preconditioner (first use)
     double* gga_ws = nullptr;     // PBE: density gradient and f_sigma-weighted gradient, 6 ng (first use)
+    // atom moves (QMD): the last three SCFs' positions and rho_out - rho_SAD (ring, newest at head - 1)
+    double* hist_drho = nullptr;  // [3][nspin * ng] (first use)
+    std::vector<double> hist_pos[3];
+    int hist_count = 0, hist_head = 0;
+    bool warm_start = false;      // the next SCF starts from kept orbitals (one filter pass first)
+    double last_alfe[2] = {0.0, 0.0};
     bool user_density = false;
     void* mlp_scratch = nullptr;  // learned guess: features [ng][32] bf16 + output [ng] (allocated on first use)
 
@@ -249,6 +255,8 @@ namespace sdft {
 
 // allocation through the context's callbacks
 void* ctx_alloc(sdft_ctx* c, size_t bytes);
+// release one allocation made by ctx_alloc (stream-ordered through the callbacks, else cudaFree)
+void ctx_release(sdft_ctx* c, void* p);
 void ctx_free_all(sdft_ctx* c);
 inline void count_launch(sdft_ctx* c, int n = 1) { c->launches += n; }
 inline size_t block_elems_bytes(const sdft_ctx* c, int precision, bool cplx, int ncol) {
@@ -300,6 +308,12 @@ void check_stencil_flag(sdft_ctx* c);
 
 // ---- kb.cu ---------------------------------------------------------------------------
 void build_kb_tables(sdft_ctx* c, int kpt);
+void release_kb_tables(sdft_ctx* c, int kpt);
+
+// ---- qmd.cu: atom moves and the extrapolated start of the next SCF ----------------------
+void push_scf_history(sdft_ctx* c);
+void move_atoms(sdft_ctx* c, const double* pos, int guess);
+void host_energy_constants(sdft_ctx* c);
 
 // ---- gridops.cu ----------------------------------------------------------------------
 void build_pseudocharge_and_sad(sdft_ctx* c);

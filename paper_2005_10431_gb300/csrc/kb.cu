@@ -251,7 +251,17 @@ void build_kb_tables(sdft_ctx* c, int kpt) {
                                                                                   T.pval64, T.pval32);
         SDFT_CUDA(cudaGetLastError());
         count_launch(c, 2);
+        ctx_release(c, pfill);
     }
+    ctx_release(c, dboxes);
+}
+
+void release_kb_tables(sdft_ctx* c, int kpt) {
+    KBTables& T = c->kb[kpt];
+    for (void* p : {(void*)T.cnt, (void*)T.idx, (void*)T.img, (void*)T.val64, (void*)T.val32, (void*)T.gamma,
+                    (void*)T.pcnt, (void*)T.patom, (void*)T.pval64, (void*)T.pval32})
+        ctx_release(c, p);
+    T = KBTables{};
 }
 
 }  // namespace sdft

@@ -294,6 +294,7 @@ void reset_state(sdft_ctx* c) {
         seed_orbitals(c, c->opt.precision, P.cplx, P.X, c->opt.nstates, problem_seed(c, P.spin, P.kpt));
         P.have_bounds = false;
     }
+    c->warm_start = false;
     c->mix_k = 0;
     c->mix_count = 0;
     c->mix_head = 0;
@@ -609,13 +610,18 @@ struct ScfRun {
         if (ev_it) cudaEventDestroy(ev_it);
     }
 
-    int passes() const { return it == 0 ? std::max(1, c->opt.first_scf_filter_passes) : 1; }
+    // several filter passes at the first V_eff (paper Sec. 2.1), one when the orbitals of the previous
+    // MD step start the run
+    int passes() const { return (it == 0 && !warm) ? std::max(1, c->opt.first_scf_filter_passes) : 1; }
+    bool warm = false;
 
     void begin() {
         ng = c->ng;
         nsp = c->opt.nspin;
         nv = nsp * ng;
         prec = c->opt.precision;
+        warm = c->warm_start;
+        c->warm_start = false;
         c->log.clear();
         ftmp = c->work64 + 20 * ng;   // rho_tot + b
         etmp = c->work64 + 21 * ng;   // two grid vectors for energies
@@ -780,6 +786,7 @@ struct ScfRun {
         if (!have64)
             for (Problem& P : c->probs) convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, ns);
         forces_compute(c);
+        push_scf_history(c);
         resolve_timing(c);
         if (out) {
             out->energy = E.F;

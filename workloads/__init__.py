@@ -228,6 +228,20 @@ def qmd_lattice8_cell(seed: int, sigma: float = 0.15) -> Cell:
     return c
 
 
+def qmd_trajectory(pos0: np.ndarray, nsteps: int, amplitude: float = 0.15, seed: int = 0,
+                   steps_per_period: float = 24.0) -> list:
+    """Smooth synthetic trajectory for QMD-style tests: atom a moves as
+    R_a(t) = R_a(0) + A_a (sin(w_a t + p_a) - sin(p_a)), with amplitudes A_a ~ N(0, amplitude^2) per
+    component, angular frequencies w_a = 2 pi / steps_per_period * u_a, u_a uniform in [0.8, 1.2], and
+    phases p_a uniform in [0, 2 pi), all from numpy's default_rng(seed).  Returns nsteps (natom, 3) arrays."""
+    rng = np.random.default_rng(seed)
+    n = pos0.shape[0]
+    amp = rng.normal(0.0, amplitude, size=(n, 3))
+    w = 2.0 * np.pi / steps_per_period * rng.uniform(0.8, 1.2, size=(n, 3))
+    ph = rng.uniform(0.0, 2.0 * np.pi, size=(n, 3))
+    return [pos0 + amp * (np.sin(w * t + ph) - np.sin(ph)) for t in range(nsteps)]
+
+
 MLP_NFEAT, MLP_HIDDEN = 32, 64
 MLP_NPARAM = MLP_HIDDEN * MLP_NFEAT + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
 
