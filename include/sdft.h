@@ -56,6 +56,7 @@ typedef int sdft_status;
 enum { SDFT_FP64 = 0, SDFT_MIXED = 1 };
 enum { SDFT_GUESS_SAD = 0, SDFT_GUESS_USER = 1 };
 enum { SDFT_XC_LDA_PZ = 0, SDFT_XC_GGA_PBE = 1 };
+enum { SDFT_BC_PERIODIC = 0, SDFT_BC_DIRICHLET = 1 };
 
 typedef struct sdft_ctx sdft_ctx;
 
@@ -120,6 +121,11 @@ typedef struct {
                                   channel through a screened-Poisson AAR solve; 0: plain Pulay */
     int xc;                    /* exchange-correlation: SDFT_XC_LDA_PZ (Perdew-Zunger LDA, paper Sec. 3) or
                                   SDFT_XC_GGA_PBE (PBE GGA, paper Sec. 2.2; nspin = 1 only) */
+    int boundary;              /* SDFT_BC_PERIODIC, or SDFT_BC_DIRICHLET for an isolated system (paper Sec. 2,
+                                  2.1): orbitals zero outside the grid, no periodic images of the atoms, and the
+                                  electrostatic potential in the 6 ghost layers beyond each face given by the
+                                  multipole expansion (l <= 6, about the centre of the grid box) of rho + b.
+                                  Gamma point and SDFT_FP64 only */
 } sdft_options;
 
 /* Per-iteration record of the SCF (paper Sec. 2.1 ".out" progress). */
@@ -298,7 +304,8 @@ sdft_status sdft_rotate(sdft_ctx* ctx, int kpt, int precision, const void* y, co
                         void* x, int ncol);
 
 /* Poisson: -L phi = 4 pi (f - mean f), zero-mean phi, by AAR (paper Sec. 2.1; Pratapa,
- * Suryanarayana & Pask 2016).  f, phi: device FP64 [ngrid]; phi is also the initial guess.
+ * Suryanarayana & Pask 2016).  For SDFT_BC_DIRICHLET contexts: -L phi = 4 pi f inside the grid with the
+ * multipole boundary values of f in the ghost layers (no mean removal, phi -> 0 far away).  f, phi: device FP64 [ngrid]; phi is also the initial guess.
  * tol bounds the FP64 relative residual.  FP64 contexts iterate in FP64; SDFT_MIXED contexts use
  * FP64 residuals with FP32 AAR correction solves (iterative refinement), same tolerance.
  * *iters receives the (inner) iteration count.  NOT_CONVERGED if the tolerance is not reached. */
@@ -336,6 +343,10 @@ sdft_status sdft_fermi(sdft_ctx* ctx, const double* eig, double* occ, double* mu
 /* Spectrum bounds by Lanczos on problem (spin, kpt): lower Ritz value, upper bound. Host out. */
 sdft_status sdft_lanczos_bounds(sdft_ctx* ctx, int spin, int kpt, int steps, double* lower,
                                 double* upper);
+
+/* Counts of the refined subspace eigensolves (FP32 solve + FP64 refinement, see sdft_subspace_eig) on this
+ * context since creation: accepted, and rejected by the device-side check and redone by cuSOLVER. */
+sdft_status sdft_get_eig_stats(const sdft_ctx* ctx, int* refined_accepted, int* refined_rejected);
 
 /* Number of kernel launches the library has issued on this context (for benchmarks). */
 sdft_status sdft_launch_count(const sdft_ctx* ctx, uint64_t* count);

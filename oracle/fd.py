@@ -47,17 +47,24 @@ def bloch_pad(u: np.ndarray, axis: int, p: int, phase: complex) -> np.ndarray:
     return v
 
 
-def laplacian(u: np.ndarray, h: tuple, phases=(1.0, 1.0, 1.0), p: int = FD_RADIUS) -> np.ndarray:
+def laplacian(u: np.ndarray, h: tuple, phases=(1.0, 1.0, 1.0), p: int = FD_RADIUS,
+              dirichlet: bool = False) -> np.ndarray:
     """(L_h u)(x) = sum_d sum_{r=-p..p} w_|r| u(x + r h_d e_d) / h_d^2.
 
     u has shape (..., n3, n2, n1) with x (d = 0) the last axis.  phases[d] is the Bloch
-    factor exp(i k_d L_d) applied when a shift wraps around the cell along d."""
+    factor exp(i k_d L_d) applied when a shift wraps around the cell along d.  dirichlet: u is zero
+    outside the grid (isolated systems) instead of periodic."""
     w = fd_weights(p)
     out = np.zeros_like(u, dtype=np.result_type(u, *[np.asarray(ph) for ph in phases]))
     for d in range(3):
         axis = u.ndim - 1 - d
         n = u.shape[axis]
-        pad = bloch_pad(u, axis, p, phases[d])
+        if dirichlet:
+            widths = [(0, 0)] * u.ndim
+            widths[axis] = (p, p)
+            pad = np.pad(u, widths)
+        else:
+            pad = bloch_pad(u, axis, p, phases[d])
         acc = w[0] * u
 
         def sl(a, b):

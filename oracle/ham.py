@@ -37,9 +37,11 @@ def kinetic(cell, X, kred=(0.0, 0.0, 0.0)):
     n1, n2, n3 = cell.n
     ph = bloch_phases(kred)
 
+    dirichlet = getattr(cell, "boundary", "periodic") == "dirichlet"
+
     def work(lo, hi):
         u = X[lo:hi].reshape(hi - lo, n3, n2, n1)
-        return lo, -0.5 * fd.laplacian(u, cell.h, ph).reshape(hi - lo, -1)
+        return lo, -0.5 * fd.laplacian(u, cell.h, ph, dirichlet=dirichlet).reshape(hi - lo, -1)
 
     out = np.empty(X.shape, dtype=np.result_type(X, complex) if any(k != 0 for k in kred) else X.dtype)
     chunk = max(1, -(-ns // (4 * (os.cpu_count() or 1))))
@@ -71,6 +73,7 @@ def dense_h(cell, V, P, E, kred=(0.0, 0.0, 0.0)):
     N = cell.ngrid
     ph = bloch_phases(kred)
     cplx = any(k != 0 for k in kred)
+    dirichlet = getattr(cell, "boundary", "periodic") == "dirichlet"
     H = np.zeros((N, N), complex if cplx else float)
     for k in range(n3):
         for j in range(n2):
@@ -83,6 +86,8 @@ def dense_h(cell, V, P, E, kred=(0.0, 0.0, 0.0)):
                         q = list(base)
                         q[d] = base[d] + r
                         wraps = q[d] // cell.n[d]
+                        if dirichlet and wraps != 0:
+                            continue          # zero outside an isolated cell
                         q[d] = q[d] % cell.n[d]
                         gq = q[0] + n1 * (q[1] + n2 * q[2])
                         H[g, gq] += -0.5 * w[abs(r)] * inv_h2 * (ph[d] ** wraps)

@@ -43,6 +43,13 @@ def _images(center, rcut, L):
     return itertools.product(*rng)
 
 
+def _cell_images(cell, center, rcut):
+    """Periodic images of an atom-centred sum; an isolated (Dirichlet) cell has the atom itself only."""
+    if getattr(cell, "boundary", "periodic") == "dirichlet":
+        return [(0, 0, 0)]
+    return _images(center, rcut, cell.L)
+
+
 def _ball_points(cell, c, rcut, strict):
     """Grid points of the cell within rcut of the point c (no wrapping): returns
     (flat indices, displacement vectors x - c)."""
@@ -73,7 +80,7 @@ def _sum_gaussians(cell, amp_of, width_of, cut_factor):
     for a in range(cell.natom):
         w = width_of(a)
         rcut = cut_factor * w
-        for t in _images(cell.pos[a], rcut, L):
+        for t in _cell_images(cell, cell.pos[a], rcut):
             c = cell.pos[a] + np.array(t) * np.array(L)
             idx, disp = _ball_points(cell, c, rcut, strict=False)
             if idx is None or idx.size == 0:
@@ -98,7 +105,7 @@ def pseudocharge_gradient(cell, a: int) -> tuple:
     amp = -s.Z * (2 * np.pi * s.r_loc ** 2) ** -1.5
     rcut = B_CUTOFF_FACTOR * s.r_loc
     out = np.zeros((3, cell.ngrid))
-    for t in _images(cell.pos[a], rcut, cell.L):
+    for t in _cell_images(cell, cell.pos[a], rcut):
         c = cell.pos[a] + np.array(t) * np.array(cell.L)
         idx, disp = _ball_points(cell, c, rcut, strict=False)
         if idx is None or idx.size == 0:
@@ -132,7 +139,7 @@ def projectors(cell, kred=(0.0, 0.0, 0.0)) -> sp.csr_matrix:
     cplx = any(abs(k) > 0 for k in kred)
     for a in range(cell.natom):
         s = cell.species[cell.types[a]]
-        for t in _images(cell.pos[a], s.r_cut_proj, cell.L):
+        for t in _cell_images(cell, cell.pos[a], s.r_cut_proj):
             c = cell.pos[a] + np.array(t) * np.array(cell.L)
             idx, disp = _ball_points(cell, c, s.r_cut_proj, strict=True)
             if idx is None or idx.size == 0:
@@ -156,7 +163,7 @@ def projector_gradients(cell, kred=(0.0, 0.0, 0.0)) -> list:
         rows, cols, vals = [], [], []
         for a in range(cell.natom):
             s = cell.species[cell.types[a]]
-            for t in _images(cell.pos[a], s.r_cut_proj, cell.L):
+            for t in _cell_images(cell, cell.pos[a], s.r_cut_proj):
                 c = cell.pos[a] + np.array(t) * np.array(cell.L)
                 idx, disp = _ball_points(cell, c, s.r_cut_proj, strict=True)
                 if idx is None or idx.size == 0:
@@ -184,6 +191,8 @@ def self_energy(cell) -> float:
 
 
 def _pair_images(cell, rmax):
+    if getattr(cell, "boundary", "periodic") == "dirichlet":
+        return [(0, 0, 0)]
     n = [int(math.ceil(rmax / cell.L[d])) + 1 for d in range(3)]
     return itertools.product(range(-n[0], n[0] + 1), range(-n[1], n[1] + 1), range(-n[2], n[2] + 1))
 

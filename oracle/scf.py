@@ -19,7 +19,7 @@ import time
 import numpy as np
 
 import workloads
-from . import chefsi, gga, ham, model, xc
+from . import chefsi, gga, ham, isolated, model, xc
 
 
 class PulayMixer:
@@ -91,7 +91,10 @@ class Problem:
     def potentials(self, rho):
         """V_eff^s = phi + V_xc^s (Sec. 2.1); returns (veff (nspin, ngrid), phi, exc per electron)."""
         rho_tot = rho.sum(axis=0)
-        phi = ham.poisson_exact(self.cell, rho_tot + self.b)
+        if getattr(self.cell, "boundary", "periodic") == "dirichlet":
+            phi = isolated.poisson_isolated(self.cell, rho_tot + self.b)
+        else:
+            phi = ham.poisson_exact(self.cell, rho_tot + self.b)
         if getattr(self.cell, "xc", "lda_pz") == "gga_pbe":
             if self.cell.nspin != 1:
                 raise ValueError("the PBE oracle is spin-unpolarized")

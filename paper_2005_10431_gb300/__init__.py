@@ -12,7 +12,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (SDFT_FP64, SDFT_MIXED, SDFT_GUESS_SAD, SDFT_GUESS_USER, SDFT_XC_LDA_PZ, SDFT_XC_GGA_PBE, sdft_options,  # noqa: F401
+from ._lib import (SDFT_FP64, SDFT_MIXED, SDFT_GUESS_SAD, SDFT_GUESS_USER, SDFT_XC_LDA_PZ, SDFT_XC_GGA_PBE, SDFT_BC_PERIODIC, SDFT_BC_DIRICHLET, sdft_options,  # noqa: F401
                    sdft_iter_record, sdft_result, SDFT_MLP_NFEAT, SDFT_MLP_NPARAM)
 
 __all__ = [
@@ -21,7 +21,7 @@ __all__ = [
     "sdft_set_density", "sdft_get_forces", "sdft_get_scf_log", "sdft_get_pseudocharge", "sdft_get_sad_density",
     "sdft_set_orbitals", "sdft_get_orbitals", "sdft_set_veff", "sdft_apply_h", "sdft_chebyshev_filter",
     "sdft_rayleigh_ritz", "sdft_subspace_matrices", "sdft_subspace_matrices_noalloc", "sdft_subspace_eig", "sdft_chebyshev_filter_multi", "sdft_rotate", "sdft_poisson", "sdft_lda", "sdft_fermi",
-    "sdft_lanczos_bounds", "sdft_kerker", "sdft_mix_step", "sdft_move_atoms", "sdft_get_input_density", "sdft_launch_count", "sdft_get_stencil_variant", "sdft_set_timing", "sdft_get_kernel_stats",
+    "sdft_lanczos_bounds", "sdft_kerker", "sdft_mix_step", "sdft_move_atoms", "sdft_get_input_density", "sdft_get_eig_stats", "sdft_launch_count", "sdft_get_stencil_variant", "sdft_set_timing", "sdft_get_kernel_stats",
     "sdft_reset_kernel_stats", "pack_block", "unpack_block", "block_shape",
     "SDFT_MLP_NFEAT", "SDFT_MLP_NPARAM", "sdft_mlp_dataset", "sdft_mlp_loss_grad", "sdft_mlp_adam",
     "sdft_mlp_train", "sdft_mlp_forward", "sdft_mlp_predict",
@@ -329,6 +329,13 @@ def sdft_move_atoms(ctx: Context, pos, guess: int = 1):
     coef = np.zeros(2)
     _check(_lib.lib().sdft_move_atoms(ctx.handle, p.ctypes.data, guess, coef.ctypes.data), ctx.handle)
     return float(coef[0]), float(coef[1])
+
+
+def sdft_get_eig_stats(ctx: Context):
+    """(accepted, rejected) refined subspace eigensolves on this context."""
+    a, r = C.c_int(0), C.c_int(0)
+    _check(_lib.lib().sdft_get_eig_stats(ctx.handle, C.byref(a), C.byref(r)), ctx.handle)
+    return a.value, r.value
 
 
 def sdft_get_input_density(ctx: Context) -> np.ndarray:

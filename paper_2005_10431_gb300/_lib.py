@@ -24,6 +24,8 @@ SDFT_GUESS_SAD = 0
 SDFT_GUESS_USER = 1
 SDFT_XC_LDA_PZ = 0
 SDFT_XC_GGA_PBE = 1
+SDFT_BC_PERIODIC = 0
+SDFT_BC_DIRICHLET = 1
 
 ERROR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "CHOLESKY",
                -6: "DEVICE_TIMEOUT", -7: "NONFINITE"}
@@ -54,7 +56,7 @@ class sdft_options(C.Structure):
         ("precision", C.c_int), ("final_fp64_pass", C.c_int), ("poisson_tol", C.c_double),
         ("init_guess", C.c_int), ("initial_moment", C.c_double), ("seed", C.c_uint64),
         ("batch_problems", C.c_int), ("use_graphs", C.c_int), ("kerker_k0", C.c_double),
-        ("xc", C.c_int),
+        ("xc", C.c_int), ("boundary", C.c_int),
     ]
 
 
@@ -121,6 +123,7 @@ SIGNATURES = {
     "sdft_kerker": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int]),
     "sdft_mix_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sdft_move_atoms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "sdft_get_eig_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "sdft_get_input_density": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]),
     "sdft_lanczos_bounds": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]),

@@ -135,7 +135,7 @@ void host_energy_constants(sdft_ctx* c) {
     c->dEsc.assign(3 * c->natom, 0.0);
     const double rmax = 30.0;
     int nimg[3];
-    for (int d = 0; d < 3; ++d) nimg[d] = (int)std::ceil(rmax / c->L[d]) + 1;
+    for (int d = 0; d < 3; ++d) nimg[d] = c->opt.boundary == SDFT_BC_DIRICHLET ? 0 : (int)std::ceil(rmax / c->L[d]) + 1;
     for (int a = 0; a < c->natom; ++a) {
         const sdft_pseudo& sa = c->species[c->types[a]];
         for (int b = 0; b < c->natom; ++b) {
@@ -366,6 +366,10 @@ sdft_status sdft_create(const sdft_cell* cell, const sdft_grid* grid, const sdft
                      "kerker_k0 must be finite and >= 0");
         SDFT_REQUIRE(o.xc == SDFT_XC_LDA_PZ || (o.xc == SDFT_XC_GGA_PBE && o.nspin == 1), SDFT_ERR_INVALID_ARG,
                      "xc must be SDFT_XC_LDA_PZ, or SDFT_XC_GGA_PBE with nspin = 1");
+        SDFT_REQUIRE(o.boundary == SDFT_BC_PERIODIC ||
+                         (o.boundary == SDFT_BC_DIRICHLET && o.precision == SDFT_FP64 && o.nkpt == 1 &&
+                          (!o.kpts || (o.kpts[0] == 0.0 && o.kpts[1] == 0.0 && o.kpts[2] == 0.0))),
+                     SDFT_ERR_INVALID_ARG, "boundary: SDFT_BC_DIRICHLET needs SDFT_FP64 and the Gamma point only");
         SDFT_REQUIRE(o.pulay_period >= 1, SDFT_ERR_INVALID_ARG, "pulay_period must be >= 1");
         SDFT_REQUIRE(o.max_scf >= 1, SDFT_ERR_INVALID_ARG, "max_scf must be >= 1");
         c->opt = o;
@@ -520,6 +524,13 @@ sdft_status sdft_move_atoms(sdft_ctx* c, const double* pos, int guess, double* c
         }
         SDFT_CUDA(cudaStreamSynchronize(c->stream));
     })
+}
+
+sdft_status sdft_get_eig_stats(const sdft_ctx* c, int* refined_accepted, int* refined_rejected) {
+    if (!c) return SDFT_ERR_INVALID_ARG;
+    if (refined_accepted) *refined_accepted = c->reig_accepted;
+    if (refined_rejected) *refined_rejected = c->reig_fallbacks;
+    return SDFT_OK;
 }
 
 sdft_status sdft_get_input_density(sdft_ctx* c, double* dst, size_t n, int on_device) {

@@ -422,7 +422,10 @@ void generalized_eig(sdft_ctx* c, bool cplx, double* M, double* Hs, double* eig,
     if (!cplx && refined_eig_supported(ncol) &&
         (c->eig_method == 2 || (c->eig_method < 0 && c->opt.precision == SDFT_MIXED))) {
         // FP32 solve refined to FP64 accuracy; verified on the device, else redone by cuSOLVER
-        if (refined_generalized_eig(c, M, Hs, Hs, eig, ncol)) return;
+        if (refined_generalized_eig(c, M, Hs, Hs, eig, ncol)) {
+            ++c->reig_accepted;
+            return;
+        }
         if (c->eig_method == 2)
             throw Error{(c->reig_last_status & 1) ? SDFT_ERR_CHOLESKY : SDFT_ERR_NONFINITE,
                         "refined subspace eigensolver rejected its result (status " +

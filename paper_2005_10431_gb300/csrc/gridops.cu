@@ -22,14 +22,14 @@ struct AtomG {
 };
 
 __device__ double image_sum(double x, double y, double z, const double* pos, double L1, double L2, double L3,
-                            double amp, double w, double cut) {
+                            double amp, double w, double cut, int isolated) {
     double s = 0.0;
     const double L[3] = {L1, L2, L3};
     const double X[3] = {x, y, z};
     int tlo[3], thi[3];
     for (int d = 0; d < 3; ++d) {
-        tlo[d] = (int)ceil((X[d] - pos[d] - cut) / L[d]);
-        thi[d] = (int)floor((X[d] - pos[d] + cut) / L[d]);
+        tlo[d] = isolated ? 0 : (int)ceil((X[d] - pos[d] - cut) / L[d]);   // isolated: the atom itself only
+        thi[d] = isolated ? 0 : (int)floor((X[d] - pos[d] + cut) / L[d]);
     }
     const double inv = 1.0 / (2.0 * w * w);
     for (int t2 = tlo[2]; t2 <= thi[2]; ++t2)
@@ -44,15 +44,15 @@ __device__ double image_sum(double x, double y, double z, const double* pos, dou
 
 __global__ void setup_fields_kernel(const AtomG* __restrict__ at, int natom, int n1, int n2, int n3, double h1,
                                     double h2, double h3, double L1, double L2, double L3, double* __restrict__ b,
-                                    double* __restrict__ sad) {
+                                    double* __restrict__ sad, int isolated) {
     const long long ng = (long long)n1 * n2 * n3;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(g % n1), j = (int)((g / n1) % n2), k = (int)(g / ((long long)n1 * n2));
         const double x = i * h1, y = j * h2, z = k * h3;
         double sb = 0.0, ss = 0.0;
         for (int a = 0; a < natom; ++a) {
-            sb += image_sum(x, y, z, at[a].pos, L1, L2, L3, at[a].amp_b, at[a].w_b, at[a].cut_b);
-            ss += image_sum(x, y, z, at[a].pos, L1, L2, L3, at[a].amp_s, at[a].w_s, at[a].cut_s);
+            sb += image_sum(x, y, z, at[a].pos, L1, L2, L3, at[a].amp_b, at[a].w_b, at[a].cut_b, isolated);
+            ss += image_sum(x, y, z, at[a].pos, L1, L2, L3, at[a].amp_s, at[a].w_s, at[a].cut_s, isolated);
         }
         b[g] = sb;
         sad[g] = ss;
@@ -493,7 +493,7 @@ __global__ void fermi_kernel(const double* __restrict__ eig, const double* __res
 // local part per atom: -dV sum_x (x - R - T)/r_loc^2 b_a(x - R - T) phi(x); one CTA per atom
 __global__ void force_local_kernel(const AtomG* __restrict__ at, int n1, int n2, int n3, double h1, double h2,
                                    double h3, double L1, double L2, double L3, double dV,
-                                   const double* __restrict__ phi, double* __restrict__ F) {
+                                   const double* __restrict__ phi, double* __restrict__ F, int isolated) {
     const int a = blockIdx.x;
     const AtomG A = at[a];
     const double cut = A.cut_b;
@@ -512,6 +512,7 @@ __global__ void force_local_kernel(const AtomG* __restrict__ at, int n1, int n2,
         const double dx = I[0] * h1 - A.pos[0], dy = I[1] * h2 - A.pos[1], dz = I[2] * h3 - A.pos[2];
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 > cut * cut) continue;
+        if (isolated && (I[0] < 0 || I[0] >= n1 || I[1] < 0 || I[1] >= n2 || I[2] < 0 || I[2] >= n3)) continue;
         const int g0 = ((I[0] % n1) + n1) % n1, g1 = ((I[1] % n2) + n2) % n2, g2 = ((I[2] % n3) + n3) % n3;
         const double ph = phi[((long long)g2 * n2 + g1) * n1 + g0];
         const double bv = A.amp_b * exp(-r2 * inv);
@@ -663,7 +664,7 @@ void build_pseudocharge_and_sad(sdft_ctx* c) {
     SDFT_CUDA(cudaMemcpyAsync(dat, at.data(), sizeof(AtomG) * c->natom, cudaMemcpyHostToDevice, c->stream));
     setup_fields_kernel<<<nblocks(c->ng), 256, 0, c->stream>>>(dat, c->natom, c->n[0], c->n[1], c->n[2], c->h[0],
                                                               c->h[1], c->h[2], c->L[0], c->L[1], c->L[2], c->b,
-                                                              c->rho_sad);
+                                                              c->rho_sad, c->opt.boundary == SDFT_BC_DIRICHLET);
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);
     // normalise the SAD density to N_e: sum rho = rho . 1
@@ -874,7 +875,7 @@ struct LapCoef {
 template <typename T>
 __global__ void __launch_bounds__(256) laplacian_residual_kernel(const T* __restrict__ x, const T* __restrict__ b,
                                                                  T* __restrict__ out, LapCoef K, int n1, int n2,
-                                                                 int n3, T shift) {
+                                                                 int n3, T shift, int dirichlet) {
     // 32-bit indices: the grid has < 2^31 points
     const int plane = n1 * n2;
     const int ng = plane * n3;
@@ -895,9 +896,15 @@ __global__ void __launch_bounds__(256) laplacian_residual_kernel(const T* __rest
         jm += jm < 0 ? n2 : 0;
         kp -= kp >= n3 ? n3 : 0;
         km += km < 0 ? n3 : 0;
-        acc += (T)K.c[0][r] * (x[row + ip] + x[row + im]);
-        acc += (T)K.c[1][r] * (x[col + jp * n1] + x[col + jm * n1]);
-        acc += (T)K.c[2][r] * (x[pl + kp * plane] + x[pl + km * plane]);
+        if (dirichlet) {   // zero beyond the grid (isolated systems: ghost values enter through b)
+            acc += (T)K.c[0][r] * ((i + r < n1 ? x[row + ip] : (T)0) + (i - r >= 0 ? x[row + im] : (T)0));
+            acc += (T)K.c[1][r] * ((j + r < n2 ? x[col + jp * n1] : (T)0) + (j - r >= 0 ? x[col + jm * n1] : (T)0));
+            acc += (T)K.c[2][r] * ((k + r < n3 ? x[pl + kp * plane] : (T)0) + (k - r >= 0 ? x[pl + km * plane] : (T)0));
+        } else {
+            acc += (T)K.c[0][r] * (x[row + ip] + x[row + im]);
+            acc += (T)K.c[1][r] * (x[col + jp * n1] + x[col + jm * n1]);
+            acc += (T)K.c[2][r] * (x[pl + kp * plane] + x[pl + km * plane]);
+        }
     }
     // -L x = 2 * (-1/2 L x): out = b + L x - shift x = b - 2 acc - shift x  (residual of (-L + shift) x = b)
     out[g] = b[g] - (T)2 * acc - shift * x[g];
@@ -912,8 +919,171 @@ void laplacian_residual(sdft_ctx* c, const T* x, const T* b, T* out, T shift = T
         K.c[2][r] = c->coef.cz[r];
     }
     K.c0 = c->coef.c0;
-    laplacian_residual_kernel<T><<<(unsigned)((c->ng + 255) / 256), 256, 0, c->stream>>>(x, b, out, K, c->n[0],
-                                                                                        c->n[1], c->n[2], shift);
+    laplacian_residual_kernel<T><<<(unsigned)((c->ng + 255) / 256), 256, 0, c->stream>>>(
+        x, b, out, K, c->n[0], c->n[1], c->n[2], shift, c->opt.boundary == SDFT_BC_DIRICHLET ? 1 : 0);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+}
+
+// ---------------------------------------------------------------------------------------
+// Isolated systems (paper Sec. 2, 2.1: Dirichlet boundary conditions with multipole boundary values).
+// q_lm = dV sum_g f_g r^l Y_lm about the centre of the grid box (l <= 6, real orthonormal Y_lm), and in
+// the 6 ghost layers phi = sum 4 pi / (2l + 1) q_lm Y_lm / r^(l+1); inside -L0 phi = 4 pi f + G with
+// L0 the zero-padded Laplacian and G the ghost values' share of the stencil.
+// ---------------------------------------------------------------------------------------
+namespace {
+constexpr int MP_LMAX = 6, MP_NLM = (MP_LMAX + 1) * (MP_LMAX + 1);
+
+// real orthonormal spherical harmonics of the direction (x, y, z), index l^2 + l + m (associated Legendre
+// functions by the standard three-term recurrence; any real orthonormal basis gives the same potential)
+__device__ void real_sh(double x, double y, double z, double* Y) {
+    const double r = sqrt(x * x + y * y + z * z);
+    double ct = 1.0, st = 0.0, cp = 1.0, sp = 0.0;
+    if (r > 0.0) {
+        ct = z / r;
+        const double rxy = sqrt(x * x + y * y);
+        st = rxy / r;
+        if (rxy > 0.0) {
+            cp = x / rxy;
+            sp = y / rxy;
+        }
+    }
+    double P[MP_LMAX + 1][MP_LMAX + 1];
+    P[0][0] = 1.0;
+    for (int m = 1; m <= MP_LMAX; ++m) P[m][m] = P[m - 1][m - 1] * (2 * m - 1) * st;
+    for (int m = 0; m < MP_LMAX; ++m) P[m + 1][m] = ct * (2 * m + 1) * P[m][m];
+    for (int m = 0; m <= MP_LMAX; ++m)
+        for (int l = m + 2; l <= MP_LMAX; ++l)
+            P[l][m] = ((2 * l - 1) * ct * P[l - 1][m] - (l + m - 1) * P[l - 2][m]) / (l - m);
+    double cm[MP_LMAX + 1], sm[MP_LMAX + 1];
+    cm[0] = 1.0;
+    sm[0] = 0.0;
+    for (int m = 1; m <= MP_LMAX; ++m) {
+        cm[m] = cm[m - 1] * cp - sm[m - 1] * sp;
+        sm[m] = sm[m - 1] * cp + cm[m - 1] * sp;
+    }
+    for (int l = 0; l <= MP_LMAX; ++l) {
+        double ratio = 1.0;   // (l - m)! / (l + m)!
+        for (int m = 0; m <= l; ++m) {
+            if (m > 0) ratio /= (double)((l + m) * (l - m + 1));
+            const double N = sqrt((2 * l + 1) / (4.0 * 3.14159265358979323846) * ratio);
+            if (m == 0) {
+                Y[l * l + l] = N * P[l][0];
+            } else {
+                Y[l * l + l + m] = 1.4142135623730951 * N * P[l][m] * cm[m];
+                Y[l * l + l - m] = 1.4142135623730951 * N * P[l][m] * sm[m];
+            }
+        }
+    }
+}
+
+// per-block partial moments part[block][lm] of f about the centre (c0, c1, c2)
+__global__ void __launch_bounds__(256) multipole_kernel(const double* __restrict__ f, int n1, int n2, int n3,
+                                                        double h1, double h2, double h3, double c0, double c1,
+                                                        double c2, double* __restrict__ part) {
+    __shared__ double sh[MP_NLM][8];
+    double acc[MP_NLM];
+    for (int k = 0; k < MP_NLM; ++k) acc[k] = 0.0;
+    const long long ng = (long long)n1 * n2 * n3;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(g % n1), j = (int)((g / n1) % n2), k = (int)(g / ((long long)n1 * n2));
+        const double x = i * h1 - c0, y = j * h2 - c1, z = k * h3 - c2;
+        const double r = sqrt(x * x + y * y + z * z);
+        double Y[MP_NLM];
+        real_sh(x, y, z, Y);
+        double rl = f[g];
+        for (int l = 0; l <= MP_LMAX; ++l) {
+            for (int m = -l; m <= l; ++m) acc[l * l + l + m] += rl * Y[l * l + l + m];
+            rl *= r;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < MP_NLM; ++k) {
+        double v = acc[k];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[k][warp] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < MP_NLM; k += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[k][w];
+        part[(long long)blockIdx.x * MP_NLM + k] = v;
+    }
+}
+
+__device__ double multipole_phi(const double* q, double x, double y, double z) {
+    double Y[MP_NLM];
+    real_sh(x, y, z, Y);
+    const double r = sqrt(x * x + y * y + z * z);
+    const double ir = 1.0 / r;
+    double irl = ir, v = 0.0;   // r^-(l+1)
+    for (int l = 0; l <= MP_LMAX; ++l) {
+        double s = 0.0;
+        for (int m = -l; m <= l; ++m) s += q[l * l + l + m] * Y[l * l + l + m];
+        v += 4.0 * 3.14159265358979323846 / (2 * l + 1) * s * irl;
+        irl *= ir;
+    }
+    return v;
+}
+
+// rhs = 4 pi f + G, G = sum over stencil neighbours beyond the grid of (w_r / h_d^2) phi_ghost
+// (K.c = -1/2 w_r / h_d^2, so G = -2 sum K.c phi_ghost)
+__global__ void __launch_bounds__(256) dirichlet_rhs_kernel(const double* __restrict__ f, double* __restrict__ rhs,
+                                                            const double* __restrict__ q, LapCoef K, int n1, int n2,
+                                                            int n3, double h1, double h2, double h3, double c0,
+                                                            double c1, double c2) {
+    const long long ng = (long long)n1 * n2 * n3;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+        const int I[3] = {(int)(g % n1), (int)((g / n1) % n2), (int)(g / ((long long)n1 * n2))};
+        const int n[3] = {n1, n2, n3};
+        const double h[3] = {h1, h2, h3}, cc[3] = {c0, c1, c2};
+        double v = 4.0 * 3.14159265358979323846 * f[g];
+        for (int d = 0; d < 3; ++d)
+            for (int r = 1; r <= FD_RADIUS; ++r)
+                for (int sgn = -1; sgn <= 1; sgn += 2) {
+                    const int id = I[d] + sgn * r;
+                    if (id >= 0 && id < n[d]) continue;
+                    double X[3];
+                    for (int e = 0; e < 3; ++e) X[e] = (e == d ? id : I[e]) * h[e] - cc[e];
+                    v += -2.0 * K.c[d][r] * multipole_phi(q, X[0], X[1], X[2]);
+                }
+        rhs[g] = v;
+    }
+}
+}  // namespace
+
+// rhs of the isolated Poisson problem for charge f (device [ngrid])
+static void isolated_poisson_rhs(sdft_ctx* c, const double* f, double* rhs) {
+    const int nblk = 128;
+    double* part = c->work64 + 27 * c->ng;   // nblk * 49 doubles (the grid's last scratch vector)
+    SDFT_REQUIRE((long long)nblk * MP_NLM <= c->ng, SDFT_ERR_INVALID_ARG, "isolated Poisson: grid too small");
+    double cen[3];
+    for (int d = 0; d < 3; ++d) cen[d] = 0.5 * (c->n[d] - 1) * c->h[d];
+    multipole_kernel<<<nblk, 256, 0, c->stream>>>(f, c->n[0], c->n[1], c->n[2], c->h[0], c->h[1], c->h[2], cen[0], cen[1],
+                                                  cen[2], part);
+    SDFT_CUDA(cudaGetLastError());
+    count_launch(c);
+    std::vector<double> hp((size_t)nblk * MP_NLM);
+    SDFT_CUDA(cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaStreamSynchronize(c->stream));
+    double q[MP_NLM];
+    for (int k = 0; k < MP_NLM; ++k) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += hp[(size_t)b * MP_NLM + k];
+        q[k] = c->dV * s;
+    }
+    double* dq = c->scal + 1700;   // [1700, 1749): multipole moments (free part of the scalar area)
+    std::memcpy(c->hscal + 1700, q, sizeof(q));
+    SDFT_CUDA(cudaMemcpyAsync(dq, c->hscal + 1700, sizeof(q), cudaMemcpyHostToDevice, c->stream));
+    LapCoef K;
+    for (int r = 0; r <= FD_RADIUS; ++r) {
+        K.c[0][r] = c->coef.cx[r];
+        K.c[1][r] = c->coef.cy[r];
+        K.c[2][r] = c->coef.cz[r];
+    }
+    K.c0 = c->coef.c0;
+    dirichlet_rhs_kernel<<<nblocks(c->ng), 256, 0, c->stream>>>(f, rhs, dq, K, c->n[0], c->n[1], c->n[2], c->h[0],
+                                                               c->h[1], c->h[2], cen[0], cen[1], cen[2]);
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);
 }
@@ -939,8 +1109,11 @@ int poisson_aar(sdft_ctx* c, const double* f, double* phi, double tol, int max_i
     int* slots = (int*)(c->scal + 96);
     double* ffv = c->scal + 128;
     double* part = c->scal + 4096;
-    // rhs = 4 pi (f - mean f); phi -= mean(phi)
-    {
+    const bool isolated = c->opt.boundary == SDFT_BC_DIRICHLET;
+    // rhs = 4 pi (f - mean f); phi -= mean(phi)   (isolated: rhs = 4 pi f + ghost term, no gauge)
+    if (isolated) {
+        isolated_poisson_rhs(c, f, rhs);
+    } else {
         double* ones = c->work64 + 3 * n;
         SDFT_CUDA(cudaMemsetAsync(ones, 0, sizeof(double) * n, c->stream));
         c->hscal[0] = 1.0;
@@ -1644,7 +1817,8 @@ void forces_compute(sdft_ctx* c) {
     AtomG* dat = (AtomG*)ctx_alloc(c, sizeof(AtomG) * std::max(1, na));
     SDFT_CUDA(cudaMemcpyAsync(dat, at.data(), sizeof(AtomG) * na, cudaMemcpyHostToDevice, c->stream));
     force_local_kernel<<<na, RB, 0, c->stream>>>(dat, c->n[0], c->n[1], c->n[2], c->h[0], c->h[1], c->h[2], c->L[0],
-                                                 c->L[1], c->L[2], c->dV, c->phi, dF);
+                                                 c->L[1], c->L[2], c->dV, c->phi, dF,
+                                                 c->opt.boundary == SDFT_BC_DIRICHLET);
     count_launch(c);
     std::vector<double> rp2(na);
     for (int a = 0; a < na; ++a) rp2[a] = std::pow(c->species[c->types[a]].r_proj, 2);
@@ -1671,6 +1845,9 @@ void forces_compute(sdft_ctx* c) {
     SDFT_CUDA(cudaMemcpyAsync(c->hscal, dF, sizeof(double) * 3 * na, cudaMemcpyDeviceToHost, c->stream));
     SDFT_CUDA(cudaStreamSynchronize(c->stream));
     for (int i = 0; i < 3 * na; ++i) c->forces[i] = c->hscal[i];
+    ctx_release(c, dat);   // per-call tables: released so that repeated SCFs (MD steps) do not accumulate them
+    ctx_release(c, d_rp2);
+    ctx_release(c, d_pos);
 }
 
 }  // namespace sdft

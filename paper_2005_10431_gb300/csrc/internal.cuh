@@ -147,6 +147,7 @@ struct sdft_ctx {
     double* reig_buf = nullptr;   // scratch of the refined eigensolver (allocated on first use)
     int reig_last_status = 0;     // its last status word (0 = accepted)
     int reig_fallbacks = 0;       // refined solves rejected and redone by cuSOLVER
+    int reig_accepted = 0;        // refined solves accepted
     // device pointer tables of batched launches (grown on demand) and their host staging copy
     void** ptab_dev = nullptr;
     int* pinfo_dev = nullptr;

@@ -26,7 +26,7 @@ __global__ void atom_support_kernel(const AtomBox* __restrict__ boxes, int cap, 
                                     double h1, double h2, double h3, double k1, double k2, double k3,
                                     int cplx, int* __restrict__ cnt, int* __restrict__ idx,
                                     int* __restrict__ img, double* __restrict__ val64,
-                                    float* __restrict__ val32) {
+                                    float* __restrict__ val32, int isolated) {
     const int a = blockIdx.x;
     const AtomBox B = boxes[a];
     const int total = B.dim[0] * B.dim[1] * B.dim[2];
@@ -52,6 +52,8 @@ __global__ void atom_support_kernel(const AtomBox* __restrict__ boxes, int cap, 
             const double dx = I[0] * h1 - B.pos[0], dy = I[1] * h2 - B.pos[1], dz = I[2] * h3 - B.pos[2];
             r2 = dx * dx + dy * dy + dz * dz;
             keep = r2 < B.rc * B.rc;
+            // an isolated cell has no periodic images: points beyond the grid are not wrapped back in
+            if (isolated && (I[0] < 0 || I[0] >= n1 || I[1] < 0 || I[1] >= n2 || I[2] < 0 || I[2] >= n3)) keep = false;
         }
         // ordered compaction: warp ballot + prefix over warps
         const unsigned ballot = __ballot_sync(0xffffffffu, keep);
@@ -218,7 +220,8 @@ void build_kb_tables(sdft_ctx* c, int kpt) {
         SDFT_CUDA(cudaMemcpyAsync(dboxes, boxes.data(), sizeof(AtomBox) * c->natom, cudaMemcpyHostToDevice, c->stream));
         atom_support_kernel<<<c->natom, 256, 0, c->stream>>>(dboxes, T.cap, c->n[0], c->n[1], c->n[2], c->h[0], c->h[1],
                                                             c->h[2], kred[0], kred[1], kred[2], T.cplx, T.cnt, T.idx,
-                                                            T.img, T.val64, T.val32);
+                                                            T.img, T.val64, T.val32,
+                                                            c->opt.boundary == SDFT_BC_DIRICHLET);
         SDFT_CUDA(cudaGetLastError());
         count_launch(c);
     }

@@ -48,6 +48,7 @@ CELLS = {
     "kspin_20": (workloads.kspin_small_cell, dict(tol=1e-8, max_iter=300, final_tol=None)),
     "qmd8_72": (qmd8_72, dict(tol=1e-10, max_iter=120, final_tol=1e-9, nbuffer=8, kerker_k0=0.8)),
     "two_atom_24_pbe": (two_atom_pbe, dict(tol=1e-10, max_iter=300, final_tol=1e-10)),
+    "isolated_pair_30": (workloads.isolated_pair_cell, dict(tol=1e-10, max_iter=300, final_tol=1e-10)),
 }
 
 
@@ -58,7 +59,7 @@ def main(names):
         t0 = time.time()
         r = scf.scf(cell, with_forces=True, verbose=True, **kw)
         out = dict(
-            cell=name, xc=getattr(cell, "xc", "lda_pz"),
+            cell=name, xc=getattr(cell, "xc", "lda_pz"), boundary=getattr(cell, "boundary", "periodic"),
             generator="tests/golden/make_golden.py (oracle.scf.scf, FP64 CPU)",
             scf_options=dict(dict(mix_beta=0.3, mix_hist=7, pulay_period=1, first_passes=4, lanczos_steps=20),
                              **kw),

@@ -88,6 +88,8 @@ class Cell:
     scf_tol: float = 1e-6
     seed: int = 0
     xc: str = "lda_pz"          # exchange-correlation functional: "lda_pz" or "gga_pbe" (unpolarized)
+    boundary: str = "periodic"  # "periodic", or "dirichlet" (isolated system: zero orbitals outside the grid,
+                                # electrostatic boundary values from a multipole expansion)
 
     @property
     def natom(self) -> int:
@@ -164,6 +166,16 @@ def small_cell(npts: int = 12, L: float = 4.0, natom: int = 1, seed: int = 7, ns
     pos = rng.uniform(0.0, L, size=(natom, 3))
     return Cell(f"small_{npts}", (L, L, L), (npts, npts, npts), pos, np.zeros(natom, int),
                 [Species()], nstates=nstates, cheb_degree=degree, seed=seed)
+
+
+def isolated_pair_cell() -> Cell:
+    """Isolated (Dirichlet) two-atom molecule: a 9.9 bohr box, 30^3 grid (h = 0.33), atoms 1.8 bohr apart
+    around the box centre, 8 states, degree 14."""
+    n, L = 30, 9.9
+    ctr = 0.5 * (n - 1) * L / n
+    pos = np.array([[ctr - 0.9, ctr + 0.1, ctr - 0.05], [ctr + 0.9, ctr - 0.1, ctr + 0.05]])
+    return Cell("isolated_pair_30", (L, L, L), (n, n, n), pos, np.zeros(2, int), [Species()], nstates=8,
+                cheb_degree=14, scf_tol=1e-6, seed=11, boundary="dirichlet")
 
 
 def monkhorst_pack(nk: int) -> tuple:
