@@ -13,6 +13,17 @@ degree-20 filter), the shape of the paper's O(100-500)-atom Gamma-point LDA runs
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 With N > 1 (torchrun) each rank solves its own replica (the method does not shard this cell).
+
+Probe modes (one JSON line each; used for profiling and per-kernel evidence, not the metric):
+    --probe filter   one sdft_chebyshev_filter of --degree on the workload's orbital block
+                     (constant V_eff, the cell's KB projectors); --variant K forces a stencil tile
+    --probe gemm     the tensor-core Gram and rotation at the workload's state count, timed with
+                     CUDA events, with their accuracy against FP64 products of sampled entries
+    --probe pass     one CheFSI pass (filter + Rayleigh-Ritz) after one SCF iteration from the SAD
+                     guess, split by kernel family; --oracle-pass adds the FP64 CPU oracle's cost of
+                     the same pass, timed on a slice and scaled (labelled as such)
+    --grid G         replaces the workload's grid by G^3 points (same cell, fewer points), so that
+                     a profiler capture stays small
 """
 from __future__ import annotations
 
@@ -42,16 +53,26 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="lattice64_80")
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    p.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-compare", action="store_true")
+    p.add_argument("--probe", choices=["filter", "gemm", "pass"], default=None)
+    p.add_argument("--variant", type=int, default=None)
+    p.add_argument("--degree", type=int, default=None)
+    p.add_argument("--grid", type=int, default=None)
+    p.add_argument("--kpoint", action="store_true")
+    p.add_argument("--reps", type=int, default=5)
+    p.add_argument("--oracle-pass", action="store_true")
     return p.parse_args()
 
 
-def cell_for(name):
+def cell_for(name, grid=None):
     import workloads
-    return {"lattice64_80": workloads.lattice64_cell, "two_atom_24": workloads.two_atom_cell,
-            "lattice216_120": workloads.lattice216_cell}[name]()
+    cell = {"lattice64_80": workloads.lattice64_cell, "two_atom_24": workloads.two_atom_cell,
+            "lattice216_120": workloads.lattice216_cell,
+            "kpoint8_40": lambda: workloads.kpoint_cell(4, 40)}[name]()
+    if grid:
+        cell.n = (grid, grid, grid)
+    return cell
 
 
 def golden(name):
@@ -131,7 +152,7 @@ def measured_peaks():
 
 def stencil_source_hash():
     h = hashlib.sha256()
-    for f in ("stencil_impl.cuh", "stencil_f32.cu"):
+    for f in ("stencil_impl.cuh", "stencil_f32.cu", "stencil_tma.cu"):
         h.update(open(os.path.join(ROOT, "paper_2005_10431_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -151,50 +172,132 @@ def recorded_traffic(workload, variant):
 # ---------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands, on a bounded sample of the same workload
 # ---------------------------------------------------------------------------------------
+# Solver settings that leave the fixed point unchanged (buffer states, the SCF error below which the
+# mixed run takes FP32 CUDA-core Rayleigh-Ritz GEMMs); the oracle reference of the 64-atom cell was
+# generated with the same 26 buffer states.
+SOLVER = {"lattice64_80": dict(nbuffer=26, gemm_fp32_switch_tol=4e-6),
+          "lattice216_120": dict(nbuffer=40, gemm_fp32_switch_tol=4e-6)}
 _ORACLE_CACHE = {}
 
 
-def oracle_sample(name, budget_s):
-    """Time full-block oracle H X applications on the workload (bounded), and scale to the metric:
-    the oracle's own SCF needs (passes x (degree + 1)) block applications of H until its energy is
-    within 1e-5 Ha/atom of its converged value (4 passes in the first iteration, then 1)."""
-    import numpy as np
-    import workloads
-    from oracle import ham, scf as oscf
-    if name not in _ORACLE_CACHE:
-        cell = cell_for(name)
-        _ORACLE_CACHE[name] = (cell, oscf.Problem(cell), workloads.initial_orbitals(cell.seed, cell.ngrid, cell.nstates))
-    cell, pr, X = _ORACLE_CACHE[name]
-    g = golden(name)
-    V = np.full(cell.ngrid, -0.3)
-    times = []
-    t_start = time.time()
-    while True:
-        t0 = time.time()
-        ham.apply_h(cell, X, V, pr.P[0], pr.E)
-        times.append(time.time() - t0)
-        if time.time() - t_start > budget_s or len(times) >= 3:
-            break
-    t_hx = min(times)
+def cpu_info():
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    return cores, cpu_model()
+
+
+def oracle_iterations_to_hit(g, natom):
+    """SCF iterations (first one included) the oracle reference needed until its free energy stayed
+    within 1e-5 Ha/atom of its converged value."""
     i_hit = None
-    if g is not None:
-        hist = g["history"]
-        e_ref = g["energy"]
-        for rec in hist:
-            ok = abs(rec["energy"] - e_ref) / cell.natom <= TOL_PER_ATOM
-            if ok and i_hit is None:
-                i_hit = rec["iter"]
-            elif not ok:
-                i_hit = None
-        passes = 4 + (i_hit if i_hit is not None else len(hist))
-    else:
-        passes = 4 + 40   # no oracle run recorded: an assumed 40 SCF iterations
-    n_hx = passes * (cell.cheb_degree + 1)
-    threads = os.cpu_count() or 1
-    return {"value": t_hx * n_hx, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": (f"{len(times)} full-block FP64 oracle H.X applications ({cell.ngrid} points x {cell.nstates} "
-                       f"states, best {t_hx:.2f} s) scaled by the {n_hx} block applications the oracle SCF used to "
-                       f"reach 1e-5 Ha/atom ({passes} CheFSI passes of degree {cell.cheb_degree} + RR)")}
+    for rec in g["history"]:
+        ok = abs(rec["energy"] - g["energy"]) / natom <= TOL_PER_ATOM
+        if ok and i_hit is None:
+            i_hit = int(rec["iter"])
+        elif not ok:
+            i_hit = None
+    return (i_hit if i_hit is not None else len(g["history"]) - 1) + 1
+
+
+def oracle_iteration_sample(name):
+    """One SCF iteration of the FP64 oracle (oracle/scf.py), run on the workload with the oracle
+    reference's own solver settings and timed part by part: the potentials (Poisson, XC), one block
+    application of H to the filtered block (the filter applies it `degree` times), the Rayleigh-Ritz
+    step (one more H application, Gram, generalized eigensolve, rotation), occupations + density +
+    energy, and the density mixing.  Returns the parts in seconds and the extrapolated iteration."""
+    import numpy as np
+    from oracle import chefsi, ham, kerker as okerker, scf as oscf
+    g = golden(name)
+    opts = (g or {}).get("scf_options", {})
+    cell = cell_for(name)
+    degree = int(opts.get("degree") or cell.cheb_degree)
+    nbuf = int(opts.get("nbuffer") or 0)
+    if name not in _ORACLE_CACHE:
+        t0 = time.perf_counter()
+        pr = oscf.Problem(cell)
+        blocks = oscf.initial_blocks(cell, nvec=cell.nstates + nbuf)
+        rho = oscf.initial_density(cell)
+        _ORACLE_CACHE[name] = (pr, blocks, rho, time.perf_counter() - t0)
+    pr, blocks, rho, t_setup = _ORACLE_CACHE[name]
+    X = blocks[0][0]
+    t = {}
+    t0 = time.perf_counter()
+    veff, phi, exc = pr.potentials(rho)
+    t["potentials"] = time.perf_counter() - t0
+    H = pr.apply_h(veff[0], 0)
+    t0 = time.perf_counter()
+    Y = H(X)
+    t["hx"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lam, Xr = chefsi.rayleigh_ritz(H, X)
+    t["rayleigh_ritz"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    eigs = lam[None, None, :cell.nstates]
+    mu, occ = ham.fermi_occupations(eigs, pr.kw, cell.nelec, cell.kT, pr.spin_factor)
+    ts = ham.entropy_term(occ, pr.kw, cell.kT, pr.spin_factor)
+    rho_out = ham.density([[Xr[:cell.nstates]]], occ, pr.kw, pr.dV)
+    pr.free_energy_hf(eigs, occ, rho, veff, phi, exc, ts)
+    t["density_energy"] = time.perf_counter() - t0
+    k0 = opts.get("kerker_k0")
+    mixer = (okerker.KerkerPulayMixer(cell, k0, 0.3, 7, 1, False, nchan=cell.nspin) if k0
+             else oscf.PulayMixer(0.3, 7, 1, False))
+    t0 = time.perf_counter()
+    mixer.update(rho.reshape(-1), rho_out.reshape(-1))
+    t["mixing"] = time.perf_counter() - t0
+    iteration = t["potentials"] + degree * t["hx"] + t["rayleigh_ritz"] + t["density_energy"] + t["mixing"]
+    return {"parts_s": t, "iteration_s": iteration, "degree": degree, "nbuffer": nbuf, "setup_s": t_setup,
+            "kerker_k0": k0, "cell": cell, "golden": g}
+
+
+def oracle_scf_estimate(name):
+    """The oracle's time to 1e-5 Ha/atom on the workload: one timed iteration sample scaled by the
+    number of iterations its reference run needed (labelled extrapolation), plus the extra filter
+    passes of the first iteration."""
+    smp = oracle_iteration_sample(name)
+    g, cell = smp["golden"], smp["cell"]
+    first_passes = int(g["scf_options"].get("first_passes", 4)) if g else 4
+    n_it = oracle_iterations_to_hit(g, cell.natom) if g else 40
+    pass_s = smp["degree"] * smp["parts_s"]["hx"] + smp["parts_s"]["rayleigh_ritz"]
+    value = n_it * smp["iteration_s"] + (first_passes - 1) * pass_s
+    cores, model = cpu_info()
+    p = smp["parts_s"]
+    sample = (f"extrapolated from one timed FP64 oracle SCF iteration on the full workload ({cell.ngrid} points, "
+              f"{cell.nstates}+{smp['nbuffer']} states, degree {smp['degree']}"
+              f"{', Kerker k0 ' + str(smp['kerker_k0']) if smp['kerker_k0'] else ''}): potentials "
+              f"{p['potentials']:.2f} s, H.X {p['hx']:.2f} s (x{smp['degree']}), Rayleigh-Ritz "
+              f"{p['rayleigh_ritz']:.2f} s, occupations/density/energy {p['density_energy']:.2f} s, mixing "
+              f"{p['mixing']:.2f} s = {smp['iteration_s']:.1f} s per iteration, x {n_it} iterations of the "
+              f"oracle reference run to 1e-5 Ha/atom, + {first_passes - 1} extra first-iteration passes")
+    return {"value": value, "unit": UNIT, "cores": cores, "cpu": model, "kind": "oracle", "sample": sample,
+            "sample_seconds": sum(p.values()), "iterations": n_it}
+
+
+def oracle_full_scf(name):
+    """The oracle's whole SCF on a small workload, timed to the first iteration after which its energy
+    stays within 1e-5 Ha/atom of the reference (the oracle's own history clock)."""
+    from oracle import scf as oscf
+    g = golden(name)
+    cell = cell_for(name)
+    t0 = time.perf_counter()
+    r = oscf.scf(cell, tol=cell.scf_tol)
+    total = time.perf_counter() - t0
+    e_ref = g["energy"] if g else r.energy
+    hit = None
+    for rec in r.history:
+        ok = abs(rec["energy"] - e_ref) / cell.natom <= TOL_PER_ATOM
+        if ok and hit is None:
+            hit = rec["t"]
+        elif not ok:
+            hit = None
+    cores, model = cpu_info()
+    return {"value": hit if hit is not None else total, "unit": UNIT, "cores": cores, "cpu": model, "kind": "oracle",
+            "sample": f"the whole FP64 oracle SCF of the workload, timed ({r.niter} iterations, {total:.1f} s to its "
+                      f"tolerance {cell.scf_tol:g}); value = time until the energy stays within 1e-5 Ha/atom",
+            "sample_seconds": total}
+
+
+def cpu_baseline(name):
+    return oracle_full_scf(name) if cell_for(name).ngrid * cell_for(name).nstates <= 2_000_000 else \
+        oracle_scf_estimate(name)
 
 
 # ---------------------------------------------------------------------------------------
@@ -207,22 +310,35 @@ def max_over_ranks(dist, vals, device):
 
 
 def run_reference(args, rank, world):
+    """The oracle arm: each step is one real, timed sample of the oracle's SCF on the workload (a full
+    SCF for the small cell, else one SCF iteration part by part); `value` is the extrapolated time to
+    1e-5 Ha/atom, `ms_per_step` the wall time a step actually took."""
     if rank != 0:
         return
-    cpu = oracle_sample(args.workload, args.cpu_sample_seconds)
-    steps = []
+    steps, walls, line = [], [], None
     for _ in range(args.warmup + args.steps):
-        steps.append(oracle_sample(args.workload, 1.0)["value"])
-    vals = steps[args.warmup:]
+        t0 = time.perf_counter()
+        line = cpu_baseline(args.workload)
+        walls.append(time.perf_counter() - t0)
+        steps.append(line["value"])
+    vals, wall = steps[args.warmup:], walls[args.warmup:]
     v = statistics.mean(vals)
-    cpu_line = dict(cpu, value=v)
+    cell = cell_for(args.workload)
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "l2": "inputs larger than L2"},
-           "impl": "reference", "cpu_baseline": cpu_line,
-           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(wall), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": bench_config(args.workload, cell, world), "impl": "reference",
+           "cpu_baseline": dict(line, value=v),
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "note": "value is extrapolated from the timed sample of each step (see cpu_baseline.sample); "
+                   "ms_per_step is the measured wall time of a step"}
     print(json.dumps(out), flush=True)
+
+
+def bench_config(name, cell, world):
+    return {"workload": name, "natom": cell.natom, "grid": list(cell.n), "nstates": cell.nstates,
+            "cheb_degree": cell.cheb_degree, "solver": SOLVER.get(name, {}),
+            "l2": "inputs larger than L2 (orbital blocks of hundreds of MB)", "parallelism": f"replicas{world}"}
 
 
 def run_ours(args, rank, world, dist):
@@ -241,7 +357,8 @@ def run_ours(args, rank, world, dist):
     # iterations here), so each step stops after 100 iterations even where the density tolerance
     # is not yet met
     opts = dict(nstates=cell.nstates, cheb_degree=cell.cheb_degree, precision=prec, scf_tol=cell.scf_tol,
-                max_scf=100, final_fp64_pass=1 if prec == sd.SDFT_MIXED else 0, kT=cell.kT, seed=cell.seed)
+                max_scf=100, final_fp64_pass=1 if prec == sd.SDFT_MIXED else 0, kT=cell.kT, seed=cell.seed,
+                **SOLVER.get(args.workload, {}))
     stream = torch.cuda.Stream()
     ctx = sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species, opts, stream=stream)
 
@@ -300,7 +417,8 @@ def run_ours(args, rank, world, dist):
     # the capture is one launch with Yprev; scale its DRAM bytes to the average launch of this run
     traffic = (rec["dram_bytes_per_launch"] * (st["bytes"] / max(1, st["launches"])) / rec["algorithmic_bytes"]
                if rec else None)
-    kname = ("cheb_row_kernel" if vname.startswith("row") else "cheb_step_kernel") + f" [{vname}]"
+    kname = ("cheb_slab_kernel" if vname.startswith("slab") else
+             "cheb_row_kernel" if vname.startswith("row") else "cheb_step_kernel") + f" [{vname}]"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": kname + " (fused stencil H.Y + Chebyshev 3-term update)",
             "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": 1e3 * st["seconds"] / max(1, st["launches"]),
@@ -355,9 +473,7 @@ def run_ours(args, rank, world, dist):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == sd.SDFT_MIXED else "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "natom": cell.natom, "grid": list(cell.n), "nstates": cell.nstates,
-                   "cheb_degree": cell.cheb_degree, "l2": "inputs larger than L2 (315 MB blocks)",
-                   "parallelism": f"replicas{world}"},
+        "config": bench_config(args.workload, cell, world),
         "roofline": roof,
         "e2e": {"value": statistics.mean(e2e_vals) if all(v is not None for v in e2e_vals) else None,
                 "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -374,14 +490,261 @@ def run_ours(args, rank, world, dist):
         out["value"] = None
         out["reference"] = f"oracle reference tests/golden/{args.workload}.json missing"
     if rank == 0 and not args.no_cpu_baseline and g is not None:
-        out["cpu_baseline"] = oracle_sample(args.workload, args.cpu_sample_seconds)
+        out["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:
         print(json.dumps(out, allow_nan=False), flush=True)
     sd.sdft_destroy(ctx)
 
 
+# ---------------------------------------------------------------------------------------
+# probe modes
+# ---------------------------------------------------------------------------------------
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    d = json.load(open(p)) if os.path.exists(p) else {}
+    return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "bf16_tflops": d.get("bf16_tflops", 1900.0),
+            "source": "measured" if d else "fallback"}
+
+
+def _event_ms(stream, fn, reps, flush=None):
+    """Best of `reps` CUDA-event timings of fn() on `stream` (L2 flushed before each when given)."""
+    import torch
+    best = float("inf")
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def gemm_pipe_flops(ng, ns):
+    """Tensor-pipe flops of the BF16x3 Gram and rotation as tiled by the kernels (3 split products,
+    128-row tiles; the Gram's column tiles of width w = min(128, rest) rounded up to 16, N = 2w; the
+    rotation's output blocks of nj <= 256 columns over 32-orbital K stages)."""
+    tiles = (ns + 127) // 128
+    w = [((min(128, ns - 128 * j) + 15) // 16) * 16 for j in range(tiles)]
+    gram_n = sum(2 * w[j] for i in range(tiles) for j in range(i, tiles))
+    gram = 3 * 2 * 128 * gram_n * ((ng + 31) // 32 * 32)
+    nsj = (ns + 255) // 256
+    nj = (((ns + nsj - 1) // nsj) + 15) // 16 * 16
+    rot = 3 * 2 * ((ng + 127) // 128 * 128) * nsj * nj * ((ns + 31) // 32 * 32)
+    return gram, rot
+
+
+def probe_gemm(args):
+    import numpy as np
+    import torch
+    import paper_2005_10431_gb300 as sd
+    cell = cell_for(args.workload, args.grid)
+    ns, ng = cell.nstates, cell.ngrid
+    stream = torch.cuda.Stream()
+    ctx = sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species,
+                         dict(nstates=ns, precision=sd.SDFT_MIXED), stream=stream)
+    gen = torch.Generator(device="cuda").manual_seed(1234)
+    y = torch.randn(ns // 2, ng, 2, device="cuda", generator=gen)
+    hy = torch.randn(ns // 2, ng, 2, device="cuda", generator=gen)
+    x = torch.empty_like(y)
+    m = torch.empty(ns, ns, dtype=torch.float64, device="cuda")
+    h = torch.empty_like(m)
+    # orthogonal Q from a seeded numpy QR (no torch.linalg: it loads an extra library lazily)
+    q = torch.from_numpy(np.linalg.qr(np.random.default_rng(1234).normal(size=(ns, ns)))[0].copy()).cuda()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2: inputs start cold
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        gram = lambda: sd.sdft_subspace_matrices(ctx, 0, sd.SDFT_MIXED, y, hy, m, h, ns)
+        rot = lambda: sd.sdft_rotate(ctx, 0, sd.SDFT_MIXED, y, q, x, ns)
+        gram(), rot()
+        t_gram = _event_ms(stream, gram, args.reps, flush)
+        t_rot = _event_ms(stream, rot, args.reps, flush)
+        gram(), rot()
+    torch.cuda.synchronize()
+    # accuracy on sampled rows / columns against FP64 products of the same FP32 values
+    idx = torch.tensor(sorted({0, 1, ns // 3, ns // 2, ns - 2, ns - 1}), device="cuda")
+    Y = y.double().permute(0, 2, 1).reshape(ns, ng)
+    HY = hy.double().permute(0, 2, 1).reshape(ns, ng)
+    Mref = Y[idx] @ Y.T
+    Href = Y[idx] @ HY.T
+    Mlib, Hlib = m.T[idx], h.T[idx]          # column-major storage: row i of M is column i
+    dg = torch.sqrt(torch.outer(torch.diagonal(Mref[:, idx]), (Y * Y).sum(1)))
+    gram_err = float(((Mlib - Mref).abs() / dg).max())
+    diag_err = float(((torch.diagonal(Mlib[:, idx]) - torch.diagonal(Mref[:, idx])).abs()
+                      / torch.diagonal(Mref[:, idx])).max())
+    # Hs is mirrored from its upper triangle: compare the upper entries
+    up = torch.arange(ns, device="cuda")[None, :] >= idx[:, None]
+    hs_err = float((((Hlib - Href).abs() / dg)[up]).max())
+    cols = torch.arange(0, ng, max(1, ng // 4096), device="cuda")
+    X = x.double().permute(0, 2, 1).reshape(ns, ng)[:, cols]
+    Xref = q @ Y[:, cols]                     # column-major Q: X_j = sum_k q[j][k] Y_k
+    rot_err = float((X - Xref).abs().max() / Xref.abs().max())
+    pk = peaks()
+    gp, rp = gemm_pipe_flops(ng, ns)
+    out = {"probe": "gemm", "workload": args.workload, "grid": list(cell.n), "nstates": ns,
+           "gram_ms": t_gram, "rotate_ms": t_rot,
+           "gram_alg_tflops": 4.0 * ng * ns * ns / t_gram / 1e9, "rotate_alg_tflops": 2.0 * ng * ns * ns / t_rot / 1e9,
+           "gram_pipe_frac": gp / t_gram / 1e9 / pk["bf16_tflops"], "rotate_pipe_frac": rp / t_rot / 1e9 / pk["bf16_tflops"],
+           "peak_bf16_tflops": pk["bf16_tflops"], "peak_source": pk["source"],
+           "gram_relerr": gram_err, "gram_diag_relerr": diag_err, "hs_relerr": hs_err, "rotate_relerr": rot_err,
+           "flop_units": "algorithmic: Gram 4 ng ns^2 (M and Hs, full), rotation 2 ng ns^2; pipe: BF16x3 MMAs as tiled",
+           "l2": "512 MB buffer written before each timed call"}
+    print(json.dumps(out), flush=True)
+    sd.sdft_destroy(ctx)
+
+
+def probe_filter(args):
+    import numpy as np
+    import torch
+    if args.variant is not None:
+        os.environ["SDFT_STENCIL_VARIANT"] = str(args.variant)
+    import workloads
+    import paper_2005_10431_gb300 as sd
+    cell = cell_for(args.workload, args.grid)
+    degree = args.degree or 4
+    prec = sd.SDFT_MIXED if args.precision == "mixed" else sd.SDFT_FP64
+    kpts = [(0.25, 0.125, -0.5)] if args.kpoint else None
+    ctx = sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species,
+                         dict(nstates=cell.nstates, cheb_degree=degree, precision=prec), kpts=kpts)
+    sd.sdft_set_veff(ctx, 0, np.full(cell.ngrid, -0.3))
+    X = workloads.initial_orbitals(0, cell.ngrid, cell.nstates, complex_valued=args.kpoint)
+    x = sd.pack_block(X, prec)
+    y = torch.empty_like(x)
+    sd.sdft_set_timing(ctx, True)
+    sd.sdft_chebyshev_filter(ctx, 0, 0, prec, x, y, cell.nstates, degree, 5.0, 160.0, -1.0)
+    torch.cuda.synchronize()
+    st = sd.sdft_get_kernel_stats(ctx)["stencil"]
+    vidx, vname = sd.sdft_get_stencil_variant(ctx, args.kpoint)
+    print(json.dumps({"probe": "filter", "workload": args.workload, "grid": list(cell.n), "nstates": cell.nstates,
+                      "degree": degree, "variant": [vidx, vname], "stencil_launches": st["launches"],
+                      "stencil_ms": 1e3 * st["seconds"],
+                      "stencil_gbs": st["bytes"] / st["seconds"] / 1e9 if st["seconds"] > 0 else None}), flush=True)
+
+
+def probe_pass(args):
+    import numpy as np
+    import torch
+    import paper_2005_10431_gb300 as sd
+    cell = cell_for(args.workload, args.grid)
+    ns, ng = cell.nstates, cell.ngrid
+    degree = args.degree or cell.cheb_degree
+    stream = torch.cuda.Stream()
+    ctx = sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species,
+                         dict(nstates=ns, cheb_degree=degree, precision=sd.SDFT_MIXED, max_scf=1, kT=cell.kT,
+                              seed=cell.seed), stream=stream)
+    sd.sdft_scf(ctx)          # one SCF iteration from the SAD guess: V_eff and a filtered subspace
+    dt, shape = sd.block_shape(sd.SDFT_MIXED, False, ns, ng)
+    x = torch.empty(shape, dtype=dt, device="cuda")
+    sd.sdft_get_orbitals(ctx, 0, 0, x)
+    eig0 = sd.sdft_get_eigenvalues(ctx)[0, 0]
+    lo, up = sd.sdft_lanczos_bounds(ctx, 0, 0, 20)
+    a0, a, b = float(eig0[0]), float(eig0[-1]), float(up)
+    y = torch.empty_like(x)
+    x2 = torch.empty_like(x)
+    eig = torch.empty(ns, dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def one_pass():
+        sd.sdft_chebyshev_filter(ctx, 0, 0, sd.SDFT_MIXED, x, y, ns, degree, a, b, a0)
+        sd.sdft_rayleigh_ritz(ctx, 0, 0, sd.SDFT_MIXED, y, x2, eig, ns)
+
+    with torch.cuda.stream(stream):
+        one_pass()
+        best, stats = float("inf"), None
+        for _ in range(max(1, args.reps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            sd.sdft_set_timing(ctx, True)
+            sd.sdft_reset_kernel_stats(ctx)
+            t = _event_ms(stream, one_pass, 1)
+            st = sd.sdft_get_kernel_stats(ctx)
+            sd.sdft_set_timing(ctx, False)
+            if t < best:
+                best, stats = t, st
+    pk = peaks()
+    fam = {}
+    for k, v in stats.items():
+        if v["launches"] == 0:
+            continue
+        e = {"ms": 1e3 * v["seconds"], "launches": v["launches"], "share": 1e3 * v["seconds"] / best}
+        if v["bytes"] > 0 and v["seconds"] > 0:
+            e["gbs"] = v["bytes"] / v["seconds"] / 1e9
+            e["hbm_frac"] = e["gbs"] / pk["hbm_gbs"]
+        if v["flops"] > 0 and v["seconds"] > 0:
+            e["alg_tflops"] = v["flops"] / v["seconds"] / 1e12
+        fam[k] = e
+    out = {"probe": "pass", "workload": args.workload, "grid": list(cell.n), "nstates": ns, "degree": degree,
+           "pass_ms": best, "kernels": fam, "peaks": pk,
+           "note": "one filter of the given degree + Rayleigh-Ritz (H.Y, Gram, generalized eigensolve, rotation); "
+                   "kernel times from the library's per-family CUDA-event timers, the pass time from events "
+                   "around it; the eigensolve at this size runs on " + ("cuSOLVER sygvd" if ns > 160 else
+                                                                       "the library's own solver")}
+    if args.oracle_pass:
+        out["oracle_pass"] = oracle_pass_estimate(cell, degree)
+    print(json.dumps(out), flush=True)
+    sd.sdft_destroy(ctx)
+
+
+def oracle_pass_estimate(cell, degree):
+    """FP64 CPU oracle cost of one CheFSI pass on `cell`, timed on slices and scaled: H.X on a tenth of
+    the states (linear in the states), the Gram and rotation on a tenth of the points (linear in the
+    points), the generalized eigensolve at full size."""
+    import numpy as np
+    import scipy.linalg as sla
+    import workloads
+    from oracle import chefsi, scf as oscf
+    ns, ng = cell.nstates, cell.ngrid
+    pr = oscf.Problem(cell)
+    V = np.full(ng, -0.3)
+    H = pr.apply_h(V, 0)
+    k = max(2, ns // 10)
+    X = workloads.initial_orbitals(cell.seed, ng, k)
+    t0 = time.perf_counter()
+    H(X)
+    t_hx = (time.perf_counter() - t0) * ns / k
+    npts = max(1, ng // 10)
+    Y = workloads.initial_orbitals(cell.seed + 1, npts, ns)
+    HY = workloads.initial_orbitals(cell.seed + 2, npts, ns)
+    t0 = time.perf_counter()
+    Ms = Y @ Y.T
+    Hs = Y @ HY.T
+    t_gram = (time.perf_counter() - t0) * ng / npts
+    Ms = Ms + ns * npts * np.eye(ns)
+    Hs = 0.5 * (Hs + Hs.T)
+    t0 = time.perf_counter()
+    lam, Q = sla.eigh(Hs, Ms)
+    t_eig = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    (Y.T @ Q).T
+    t_rot = (time.perf_counter() - t0) * ng / npts
+    total = (degree + 1) * t_hx + t_gram + t_eig + t_rot
+    return {"seconds": total, "hx_s": t_hx, "gram_s": t_gram, "eig_s": t_eig, "rotate_s": t_rot,
+            "cores": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count(),
+            "cpu": cpu_model(),
+            "sample": f"extrapolated: H.X timed on {k} of {ns} states, Gram and rotation on {npts} of {ng} points, "
+                      f"eigensolve at n = {ns}; pass = (degree + 1) H.X + Gram + eigensolve + rotation"}
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def main():
     args = parse()
+    if args.probe:
+        {"filter": probe_filter, "gemm": probe_gemm, "pass": probe_pass}[args.probe](args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

@@ -126,6 +126,22 @@ typedef struct {
                                   electrostatic potential in the 6 ghost layers beyond each face given by the
                                   multipole expansion (l <= 6, about the centre of the grid box) of rho + b.
                                   Gamma point and SDFT_FP64 only */
+    int nbuffer;               /* >= 0 extra orbitals per problem that are filtered and enter Rayleigh-Ritz
+                                  but are never occupied (occupations, density, energy and forces use the
+                                  lowest nstates).  The filter cutoff then sits at the top Ritz value of the
+                                  wider block, away from the partially occupied states at the top of the
+                                  nstates block, which the Chebyshev filter otherwise barely separates
+                                  (CheFSI buffer states; the fixed point is unchanged).  nstates + nbuffer
+                                  is even for SDFT_MIXED.  sdft_set/get_orbitals move the lowest nstates;
+                                  the step-level calls accept blocks of up to nstates + nbuffer columns */
+    double fp64_switch_tol;    /* SDFT_MIXED, > 0: once the SCF error falls below this, the remaining SCF
+                                  iterations run FP64 CheFSI passes on FP64 copies of the orbitals (with FP32
+                                  orbitals the density residual of the mixed path levels off near 1e-6), and
+                                  the final FP64 pass is not needed; 0: the whole SCF in mixed precision */
+    double gemm_fp32_switch_tol; /* SDFT_MIXED, > 0: once the SCF error falls below this, the Rayleigh-Ritz
+                                  GEMMs (Gram, rotation) change from BF16x3 tensor-core products (about 17
+                                  significant bits, which hold the mixed density residual near 1e-6) to FP32
+                                  CUDA-core products for the rest of the SCF; 0: tensor cores throughout */
 } sdft_options;
 
 /* Per-iteration record of the SCF (paper Sec. 2.1 ".out" progress). */
@@ -185,7 +201,8 @@ sdft_status sdft_scf(sdft_ctx* ctx, sdft_result* out);
  * contexts run their passes alone.  A context stops at its own convergence or max_scf.
  * out: host array of n results, filled for every context.  Returns the first non-OK status in
  * context order (NOT_CONVERGED if a context did not converge); an error inside any context
- * aborts the batch and is reported on ctxs[0] (and copied to the others' sdft_last_error). */
+ * aborts the batch and is reported on ctxs[0] (and copied to the others' sdft_last_error).  Two
+ * batches must not run at the same time (see the shared table of sdft_chebyshev_filter_multi). */
 sdft_status sdft_batch_scf(sdft_ctx* const* ctxs, int n, sdft_result* out);
 /* Re-seed the initial orbitals of every problem from opt.seed (as at create) and reset the
  * density guess to the SAD (or last user) density, so that sdft_scf can be repeated. */
@@ -256,7 +273,10 @@ sdft_status sdft_rayleigh_ritz(sdft_ctx* ctx, int spin, int kpt, int precision,
  * ONE column-tile stencil launch over all cells (per-cell grid, coefficients and recurrence scalars
  * in a constant-memory table) after the cells' KB projections; every cell computes exactly what
  * sdft_chebyshev_filter computes for it with the column tile.  1 <= n <= 64; all contexts must use
- * the same CUDA stream.  Returns after the work is enqueued and completed (synchronises). */
+ * the same CUDA stream.  Returns after the work is enqueued and completed (synchronises).  The
+ * per-cell table is ONE constant-memory array of the library, rewritten before every step: two
+ * multi-cell filters (this call or sdft_batch_scf) running at the same time on different streams or
+ * host threads overwrite each other's table and give wrong results; serialise them. */
 sdft_status sdft_chebyshev_filter_multi(sdft_ctx* const* ctxs, int n, const void* const* x, void* const* y,
                                         int degree, const double* a, const double* b, const double* a0);
 
@@ -273,8 +293,10 @@ sdft_status sdft_subspace_matrices(sdft_ctx* ctx, int kpt, int precision, const 
  *
  * Computes the same M = Y^H Y and Hs = Y^H (H Y) (FP64 ncol x ncol, column-major, double2 for
  * complex) from device blocks y, hy of ngrid x ncol in the storage kind of (precision,
- * is_complex), with the same kernels, enqueued on cuda_stream (a cudaStream_t, NULL = default
- * stream); no context is needed and nothing is allocated.  The split-K partial sums use a fixed
+ * is_complex), enqueued on cuda_stream (a cudaStream_t, NULL = default stream); no context is
+ * needed and nothing is allocated.  It always runs the CUDA-core Gram of the storage kind, so for
+ * real SDFT_MIXED blocks with ncol >= 32 (where sdft_subspace_matrices runs the BF16x3 tensor-core
+ * Gram) the two agree to FP32 tolerance, not bit for bit.  The split-K partial sums use a fixed
  * 32 MiB device array inside the library, so 2*ncol^2*(2 if complex) must not exceed 4194304
  * doubles (ncol <= 1448 real, <= 1024 complex); larger ncol returns SDFT_ERR_INVALID_ARG before
  * anything is launched.  The first call on each device looks up that array's device address

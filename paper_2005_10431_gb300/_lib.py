@@ -56,7 +56,8 @@ class sdft_options(C.Structure):
         ("precision", C.c_int), ("final_fp64_pass", C.c_int), ("poisson_tol", C.c_double),
         ("init_guess", C.c_int), ("initial_moment", C.c_double), ("seed", C.c_uint64),
         ("batch_problems", C.c_int), ("use_graphs", C.c_int), ("kerker_k0", C.c_double),
-        ("xc", C.c_int), ("boundary", C.c_int),
+        ("xc", C.c_int), ("boundary", C.c_int), ("nbuffer", C.c_int), ("fp64_switch_tol", C.c_double),
+        ("gemm_fp32_switch_tol", C.c_double),
     ]
 
 

@@ -168,7 +168,8 @@ namespace {
 void build_context(sdft_ctx* c) {
     const sdft_options& o = c->opt;
     const long long ng = c->ng;
-    const int ns = o.nstates;
+    const int ns = o.nstates;    // occupied set: eigenvalues and occupations reported per problem
+    const int nf = c->nfilt;      // filtered block: orbitals, Rayleigh-Ritz matrices and workspaces
     SDFT_CUDA(cudaMallocHost(&c->hscal, sizeof(double) * SCAL_DOUBLES));
     cusolverStatus_t cs = cusolverDnCreate(&c->solver);
     SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "cusolverDnCreate failed");
@@ -217,37 +218,40 @@ void build_context(sdft_ctx* c) {
             P.spin = s;
             P.kpt = k;
             P.cplx = c->kb[k].cplx;
-            const size_t bytes = block_elems_bytes(c, o.precision, P.cplx, ns);
+            const size_t bytes = block_elems_bytes(c, o.precision, P.cplx, nf);
             P.X = ctx_alloc(c, bytes);
-            if (o.precision == SDFT_MIXED) P.X64 = ctx_alloc(c, block_elems_bytes(c, SDFT_FP64, P.cplx, ns));
+            if (o.precision == SDFT_MIXED) P.X64 = ctx_alloc(c, block_elems_bytes(c, SDFT_FP64, P.cplx, nf));
             P.eig = eig_all + (long long)(s * o.nkpt + k) * ns;
+            P.eigf = nf > ns ? (double*)ctx_alloc(c, sizeof(double) * nf) : P.eig;
             P.occ = occ_all + (long long)(s * o.nkpt + k) * ns;
             maxblock = std::max(maxblock, bytes);
-            if (o.precision == SDFT_MIXED) maxblock = std::max(maxblock, block_elems_bytes(c, SDFT_FP64, P.cplx, ns));
+            if (o.precision == SDFT_MIXED) maxblock = std::max(maxblock, block_elems_bytes(c, SDFT_FP64, P.cplx, nf));
         }
     c->block_bytes = maxblock;
     for (int i = 0; i < 4; ++i) c->blk[i] = ctx_alloc(c, maxblock);
     const int w2 = any_cplx ? 2 : 1;
-    c->Ms = (double*)ctx_alloc(c, sizeof(double) * ns * ns * w2);
-    c->Hs = (double*)ctx_alloc(c, sizeof(double) * ns * ns * w2);
-    c->part_elems = std::max<size_t>((size_t)2 * ns * ns * w2 * 64, 1 << 20);
+    c->Ms = (double*)ctx_alloc(c, sizeof(double) * nf * nf * w2);
+    c->Hs = (double*)ctx_alloc(c, sizeof(double) * nf * nf * w2);
+    c->part_elems = std::max<size_t>((size_t)2 * nf * nf * w2 * 64, 1 << 20);
     c->part = (double*)ctx_alloc(c, sizeof(double) * c->part_elems);
-    c->dscale = (double*)ctx_alloc(c, sizeof(double) * ns);
-    c->Q32 = ctx_alloc(c, sizeof(float) * ns * ns * w2);
-    c->C32 = (float*)ctx_alloc(c, sizeof(float) * 2 * std::max(1, c->natom) * ns);
-    c->C64 = (double*)ctx_alloc(c, sizeof(double) * 2 * std::max(1, c->natom) * ns);
+    c->dscale = (double*)ctx_alloc(c, sizeof(double) * nf);
+    c->Q32 = ctx_alloc(c, sizeof(float) * nf * nf * w2);
+    c->qsplit_bytes = sdft::qsplit_bytes(nf);
+    c->Qsplit = ctx_alloc(c, c->qsplit_bytes);
+    c->C32 = (float*)ctx_alloc(c, sizeof(float) * 2 * std::max(1, c->natom) * nf);
+    c->C64 = (double*)ctx_alloc(c, sizeof(double) * 2 * std::max(1, c->natom) * nf);
     c->dinfo = (int*)ctx_alloc(c, sizeof(int) * 4);
-    // cuSOLVER workspace for the generalized eigenproblem of size ns
+    // cuSOLVER workspace for the generalized eigenproblem of size nf
     int lw = 0;
     if (any_cplx) {
         cs = cusolverDnZhegvd_bufferSize(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
-                                         CUBLAS_FILL_MODE_UPPER, ns, (cuDoubleComplex*)c->Hs, ns,
-                                         (cuDoubleComplex*)c->Ms, ns, c->dscale, &lw);
+                                         CUBLAS_FILL_MODE_UPPER, nf, (cuDoubleComplex*)c->Hs, nf,
+                                         (cuDoubleComplex*)c->Ms, nf, c->dscale, &lw);
         SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "hegvd workspace query failed");
         c->solver_lwork = lw;
     }
     cs = cusolverDnDsygvd_bufferSize(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER,
-                                     ns, c->Hs, ns, c->Ms, ns, c->dscale, &lw);
+                                     nf, c->Hs, nf, c->Ms, nf, c->dscale, &lw);
     SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "sygvd workspace query failed");
     c->solver_lwork = std::max(c->solver_lwork, lw);
     if (const char* env = getenv("SDFT_EIGEN")) c->eig_method = atoi(env);
@@ -258,7 +262,7 @@ void build_context(sdft_ctx* c) {
     cusolverDnXsyevjSetTolerance(c->syevj_params, 1e-14);
     cusolverDnXsyevjSetMaxSweeps(c->syevj_params, 30);
     cs = cusolverDnDsygvj_bufferSize(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER,
-                                     ns, c->Hs, ns, c->Ms, ns, c->dscale, &lw, c->syevj_params);
+                                     nf, c->Hs, nf, c->Ms, nf, c->dscale, &lw, c->syevj_params);
     SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "sygvj workspace query failed");
     c->solver_lwork = std::max(c->solver_lwork, lw);
     c->solver_work = ctx_alloc(c, (size_t)c->solver_lwork * 16 + 256);
@@ -372,7 +376,14 @@ sdft_status sdft_create(const sdft_cell* cell, const sdft_grid* grid, const sdft
                      SDFT_ERR_INVALID_ARG, "boundary: SDFT_BC_DIRICHLET needs SDFT_FP64 and the Gamma point only");
         SDFT_REQUIRE(o.pulay_period >= 1, SDFT_ERR_INVALID_ARG, "pulay_period must be >= 1");
         SDFT_REQUIRE(o.max_scf >= 1, SDFT_ERR_INVALID_ARG, "max_scf must be >= 1");
+        SDFT_REQUIRE(o.nbuffer >= 0 && (o.precision == SDFT_FP64 || o.nbuffer % 2 == 0), SDFT_ERR_INVALID_ARG,
+                     "nbuffer must be >= 0, and even for SDFT_MIXED");
+        SDFT_REQUIRE(std::isfinite(o.fp64_switch_tol) && o.fp64_switch_tol >= 0.0, SDFT_ERR_INVALID_ARG,
+                     "fp64_switch_tol must be finite and >= 0");
+        SDFT_REQUIRE(std::isfinite(o.gemm_fp32_switch_tol) && o.gemm_fp32_switch_tol >= 0.0, SDFT_ERR_INVALID_ARG,
+                     "gemm_fp32_switch_tol must be finite and >= 0");
         c->opt = o;
+        c->nfilt = o.nstates + o.nbuffer;
         c->stream = (cudaStream_t)cuda_stream;
         c->alloc = alloc;
         c->release = free_fn;
@@ -592,7 +603,7 @@ static void check_block_args(sdft_ctx* c, int spin, int kpt, int precision, int 
     SDFT_REQUIRE(spin >= 0 && spin < c->opt.nspin && kpt >= 0 && kpt < c->opt.nkpt, SDFT_ERR_INVALID_ARG,
                  "spin / k-point index out of range");
     SDFT_REQUIRE(precision == SDFT_FP64 || precision == SDFT_MIXED, SDFT_ERR_INVALID_ARG, "precision");
-    SDFT_REQUIRE(ncol >= 1 && ncol <= c->opt.nstates, SDFT_ERR_INVALID_ARG, "ncol must be in [1, nstates]");
+    SDFT_REQUIRE(ncol >= 1 && ncol <= c->nfilt, SDFT_ERR_INVALID_ARG, "ncol must be in [1, nstates + nbuffer]");
     SDFT_REQUIRE(precision == SDFT_FP64 || c->kb[kpt].cplx || ncol % 2 == 0, SDFT_ERR_INVALID_ARG,
                  "SDFT_MIXED real blocks need an even column count");
 }
@@ -845,8 +856,8 @@ sdft_status sdft_chebyshev_filter_multi(sdft_ctx* const* ctxs, int n, const void
 sdft_status sdft_subspace_eig(sdft_ctx* c, int is_complex, double* m, double* hs, double* eig, int ncol) {
     SDFT_TRY(c, {
         SDFT_REQUIRE(m && hs && eig, SDFT_ERR_INVALID_ARG, "null pointer");
-        SDFT_REQUIRE(ncol >= 1 && ncol <= c->opt.nstates, SDFT_ERR_INVALID_ARG,
-                     "ncol must be in [1, nstates] (solver workspace is sized for nstates)");
+        SDFT_REQUIRE(ncol >= 1 && ncol <= c->nfilt, SDFT_ERR_INVALID_ARG,
+                     "ncol must be in [1, nstates + nbuffer] (solver workspace is sized for it)");
         bool any_cplx = false;
         for (const auto& P : c->probs) any_cplx = any_cplx || P.cplx;
         SDFT_REQUIRE(!is_complex || any_cplx, SDFT_ERR_INVALID_ARG,

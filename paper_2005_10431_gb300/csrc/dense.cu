@@ -338,8 +338,9 @@ double* noalloc_scratch() {
 
 }  // namespace
 
-// M = Y^H Y, Hs = Y^H HY with the split-K partials in the fixed scratch above; launches the
-// same kernels as subspace_gram on `stream` and allocates nothing.
+// M = Y^H Y, Hs = Y^H HY with the split-K partials in the fixed scratch above, on `stream`, allocating
+// nothing.  Always the CUDA-core gram_kernel of the storage kind: for real mixed blocks with ncol >= 32
+// subspace_gram takes the BF16x3 tensor-core path instead, and the two agree to FP32 tolerance.
 void subspace_gram_noalloc(int precision, bool cplx, const void* Y, const void* HY, long long ng, int ncol,
                            double* M, double* Hs, cudaStream_t stream) {
     const int w = cplx ? 2 : 1;
@@ -371,7 +372,7 @@ void subspace_gram_noalloc(int precision, bool cplx, const void* Y, const void* 
 
 void subspace_gram(sdft_ctx* c, int precision, bool cplx, const void* Y, const void* HY, double* M, double* Hs,
                    int ncol) {
-    if (gram_tc_supported(precision, cplx, ncol)) {
+    if (gram_tc_supported(c, precision, cplx, ncol)) {
         subspace_gram_tc(c, Y, HY, M, Hs, ncol);
         return;
     }
@@ -389,7 +390,8 @@ void subspace_gram(sdft_ctx* c, int precision, bool cplx, const void* Y, const v
     nsplit = (c->ng + chunk - 1) / chunk;
     SDFT_REQUIRE((size_t)(nsplit * 2 * nn * w) <= c->part_elems, SDFT_ERR_INVALID_ARG, "gram: partial buffer too small");
     dim3 grid(tiles, tiles, (unsigned)nsplit);
-    ScopedTimer timer(c, SDFT_K_GRAM, 0.0, 2.0 * (double)c->ng * ncol * ncol * (cplx ? 4.0 : 1.0));
+    // algorithmic flops: two full ngrid x ncol x ncol products (M and Hs), x4 for complex
+    ScopedTimer timer(c, SDFT_K_GRAM, 0.0, 4.0 * (double)c->ng * ncol * ncol * (cplx ? 4.0 : 1.0));
     switch (kind) {
         case 0: gram_kernel<0><<<grid, 256, 0, c->stream>>>(Y, HY, ncol, c->ng, chunk, c->part); break;
         case 1: gram_kernel<1><<<grid, 256, 0, c->stream>>>(Y, HY, ncol, c->ng, chunk, c->part); break;
@@ -465,14 +467,14 @@ void rotate_block(sdft_ctx* c, int precision, bool cplx, const void* Y, const do
     dim3 grid((unsigned)((c->ng + 63) / 64), (ncol + 31) / 32);
     const void* Qp = Q;
     if (precision != SDFT_FP64) {
+        if (rotate_tc_supported(c, precision, cplx, ncol)) {
+            rotate_tc(c, Y, Q, X, ncol);
+            return;
+        }
         const long long nq = (long long)ncol * ncol * (cplx ? 2 : 1);
         to_float_kernel<<<nb(nq), 256, 0, c->stream>>>(Q, (float*)c->Q32, nq);
         count_launch(c);
         Qp = c->Q32;
-        if (rotate_tc_supported(precision, cplx, ncol)) {
-            rotate_tc(c, Y, (const float*)c->Q32, X, ncol);
-            return;
-        }
     }
     ScopedTimer timer(c, SDFT_K_ROTATE, 0.0, 2.0 * (double)c->ng * ncol * ncol * (cplx ? 4.0 : 1.0));
     switch (kind) {

@@ -112,7 +112,8 @@ struct Problem {              // one (spin, k) eigenproblem
     bool cplx = false;
     void* X = nullptr;        // current orbitals (FP64 or MIXED storage)
     void* X64 = nullptr;      // FP64 copy used by the final FP64 pass (MIXED)
-    double* eig = nullptr;    // [nstates]
+    double* eig = nullptr;    // [nstates] lowest Ritz values (occupations, energies, results)
+    double* eigf = nullptr;   // [nstates + nbuffer] Ritz values of the filtered block (== eig if no buffer)
     double* occ = nullptr;    // [nstates]
     double lower = 0, cutoff = 0, upper = 0;
     bool have_bounds = false;
@@ -130,6 +131,8 @@ struct sdft_ctx {
     std::vector<int> types;
     std::vector<sdft_pseudo> species;
     sdft_options opt{};
+    int nfilt = 0;                // filtered block width: nstates + nbuffer
+    bool gemm_fp32 = false;       // Rayleigh-Ritz GEMMs on CUDA cores in FP32 (set by the SCF's precise tail)
     std::vector<double> kpts, kw;
     double nelec = 0;
     sdft::StencilCoef coef{};
@@ -200,6 +203,8 @@ struct sdft_ctx {
     int solver_lwork = 0;
     int* dinfo = nullptr;
     void* Q32 = nullptr;          // rotation matrix in the block precision
+    void* Qsplit = nullptr;       // bf16 hi/lo rows of Q^T for the tensor-core rotation
+    size_t qsplit_bytes = 0;
     float* C32 = nullptr;         // KB coefficients [ncol * natom] (x2)
     double* C64 = nullptr;
 
@@ -342,10 +347,11 @@ void forces_compute(sdft_ctx* c);
 void subspace_gram(sdft_ctx* c, int precision, bool cplx, const void* Y, const void* HY,
                    double* M, double* Hs, int ncol);
 // tcgen05 BF16x3 path of subspace_gram for FP32 real blocks (gemm_tc.cu)
-bool gram_tc_supported(int precision, bool cplx, int ncol);
+bool gram_tc_supported(const sdft_ctx* c, int precision, bool cplx, int ncol);
 void subspace_gram_tc(sdft_ctx* c, const void* Y, const void* HY, double* M, double* Hs, int ncol);
-bool rotate_tc_supported(int precision, bool cplx, int ncol);
-void rotate_tc(sdft_ctx* c, const void* Y, const float* Q32, void* X, int ncol);
+bool rotate_tc_supported(const sdft_ctx* c, int precision, bool cplx, int ncol);
+size_t qsplit_bytes(int ncol);
+void rotate_tc(sdft_ctx* c, const void* Y, const double* Q, void* X, int ncol);
 // allocation-free variant: partials in a fixed file-scope device array (no context needed)
 void subspace_gram_noalloc(int precision, bool cplx, const void* Y, const void* HY, long long ng, int ncol,
                            double* M, double* Hs, cudaStream_t stream);

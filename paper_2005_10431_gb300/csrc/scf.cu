@@ -291,7 +291,7 @@ void reset_state(sdft_ctx* c) {
     }
     SDFT_CUDA(cudaMemsetAsync(c->phi, 0, sizeof(double) * ng, c->stream));
     for (Problem& P : c->probs) {
-        seed_orbitals(c, c->opt.precision, P.cplx, P.X, c->opt.nstates, problem_seed(c, P.spin, P.kpt));
+        seed_orbitals(c, c->opt.precision, P.cplx, P.X, c->nfilt, problem_seed(c, P.spin, P.kpt));
         P.have_bounds = false;
     }
     c->warm_start = false;
@@ -302,15 +302,22 @@ void reset_state(sdft_ctx* c) {
     SDFT_CUDA(cudaGetLastError());
 }
 
+// the occupied set's Ritz values (the lowest nstates) from the filtered block's (with buffer states)
+static void keep_lowest_ritz_values(sdft_ctx* c, Problem& P) {
+    if (P.eigf != P.eig)
+        SDFT_CUDA(cudaMemcpyAsync(P.eig, P.eigf, sizeof(double) * c->opt.nstates, cudaMemcpyDeviceToDevice, c->stream));
+}
+
 // Rayleigh-Ritz of problem P on the filtered block Y into X, and the new filter bounds
 static void rr_pass(sdft_ctx* c, Problem& P, int precision, void* Y, void* X) {
-    const int ns = c->opt.nstates;
+    const int nf = c->nfilt;
     const double* v64 = c->veff + (long long)P.spin * c->ng;
     const float* v32 = c->veff32 + (long long)P.spin * c->ng;
-    rayleigh_ritz(c, P.kpt, precision, Y, X, P.eig, ns, v64, v32);
+    rayleigh_ritz(c, P.kpt, precision, Y, X, P.eigf, nf, v64, v32);
+    keep_lowest_ritz_values(c, P);
     double e2[2];
-    SDFT_CUDA(cudaMemcpyAsync(&e2[0], P.eig, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    SDFT_CUDA(cudaMemcpyAsync(&e2[1], P.eig + ns - 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaMemcpyAsync(&e2[0], P.eigf, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SDFT_CUDA(cudaMemcpyAsync(&e2[1], P.eigf + nf - 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     SDFT_CUDA(cudaStreamSynchronize(c->stream));
     check_stencil_flag(c);
     if (!std::isfinite(e2[0]) || !std::isfinite(e2[1])) throw Error{SDFT_ERR_NONFINITE, "Ritz values are not finite"};
@@ -323,8 +330,7 @@ static void chefsi_pass(sdft_ctx* c, Problem& P, int precision, void* X) {
     const double* v64 = c->veff + (long long)P.spin * c->ng;
     const float* v32 = c->veff32 + (long long)P.spin * c->ng;
     void* Y = c->blk[0];
-    chebyshev_filter(c, P.kpt, precision, X, Y, c->opt.nstates, c->opt.cheb_degree, P.cutoff, P.upper, P.lower, v64,
-                     v32);
+    chebyshev_filter(c, P.kpt, precision, X, Y, c->nfilt, c->opt.cheb_degree, P.cutoff, P.upper, P.lower, v64, v32);
     rr_pass(c, P, precision, Y, X);
 }
 
@@ -333,7 +339,7 @@ static void chefsi_pass(sdft_ctx* c, Problem& P, int precision, void* X) {
 // problem; the H Y of Rayleigh-Ritz likewise; then Gram matrices per problem, one batched
 // eigensolve for all problems, rotations per problem, and one host read of all Ritz bounds.
 static void ensure_group_buffers(sdft_ctx* c, int nprob, bool cplx) {
-    const int ns = c->opt.nstates;
+    const int ns = c->nfilt;
     if ((int)c->g_M.size() >= nprob) return;
     const size_t bytes = block_elems_bytes(c, SDFT_MIXED, cplx, ns);
     const int w2 = cplx ? 2 : 1;
@@ -346,7 +352,7 @@ static void ensure_group_buffers(sdft_ctx* c, int nprob, bool cplx) {
 }
 
 static void chefsi_pass_group(sdft_ctx* c, const std::vector<Problem*>& G, int variant) {
-    const int ns = c->opt.nstates, m = c->opt.cheb_degree;
+    const int ns = c->nfilt, m = c->opt.cheb_degree;   // filtered block width
     const int np = (int)G.size();
     const bool cplx = G[0]->cplx;
     const int ncolE = cplx ? ns : ns / 2;
@@ -507,7 +513,7 @@ static void chefsi_pass_group(sdft_ctx* c, const std::vector<Problem*>& G, int v
         for (int p = 0; p < np; ++p) {
             c->ptab_host[p] = c->g_M[p];
             c->ptab_host[np + p] = c->g_H[p];
-            c->ptab_host[2 * np + p] = G[p]->eig;
+            c->ptab_host[2 * np + p] = G[p]->eigf;
         }
         SDFT_CUDA(cudaMemcpyAsync(c->ptab_dev, c->ptab_host.data(), sizeof(void*) * 3 * np, cudaMemcpyHostToDevice,
                                   c->stream));
@@ -519,7 +525,7 @@ static void chefsi_pass_group(sdft_ctx* c, const std::vector<Problem*>& G, int v
         for (int p = 0; p < np; ++p)
             if (info[p] != 0) throw Error{SDFT_ERR_CHOLESKY, "subspace overlap matrix not positive definite"};
     } else {
-        for (int p = 0; p < np; ++p) generalized_eig(c, cplx, c->g_M[p], c->g_H[p], G[p]->eig, ns);
+        for (int p = 0; p < np; ++p) generalized_eig(c, cplx, c->g_M[p], c->g_H[p], G[p]->eigf, ns);
     }
     for (int p = 0; p < np; ++p) {
         const RowProblem& r = c->g_rtab_h[m * np + p];
@@ -527,8 +533,9 @@ static void chefsi_pass_group(sdft_ctx* c, const std::vector<Problem*>& G, int v
     }
     std::vector<double> e2(2 * np);
     for (int p = 0; p < np; ++p) {
-        SDFT_CUDA(cudaMemcpyAsync(&e2[2 * p], G[p]->eig, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        SDFT_CUDA(cudaMemcpyAsync(&e2[2 * p + 1], G[p]->eig + ns - 1, sizeof(double), cudaMemcpyDeviceToHost,
+        keep_lowest_ritz_values(c, *G[p]);
+        SDFT_CUDA(cudaMemcpyAsync(&e2[2 * p], G[p]->eigf, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        SDFT_CUDA(cudaMemcpyAsync(&e2[2 * p + 1], G[p]->eigf + ns - 1, sizeof(double), cudaMemcpyDeviceToHost,
                                   c->stream));
     }
     SDFT_CUDA(cudaStreamSynchronize(c->stream));
@@ -601,6 +608,8 @@ struct ScfRun {
     std::vector<Problem*> groups[2], single;
     int group_var[2] = {-1, -1};
     bool batched = false;
+    // mixed run finishing in FP64 (fp64_switch_tol): CheFSI passes on the FP64 copies of the orbitals
+    bool tail64 = false;
 
     explicit ScfRun(sdft_ctx* c_) : c(c_) {}
     ScfRun(const ScfRun&) = delete;
@@ -620,6 +629,7 @@ struct ScfRun {
         nsp = c->opt.nspin;
         nv = nsp * ng;
         prec = c->opt.precision;
+        c->gemm_fp32 = false;
         warm = c->warm_start;
         c->warm_start = false;
         c->log.clear();
@@ -633,7 +643,7 @@ struct ScfRun {
         SDFT_CUDA(cudaEventRecord(ev_start, c->stream));
         if (prec == SDFT_MIXED && c->opt.batch_problems && c->probs.size() > 1) {
             for (int k = 0; k < 2; ++k) {
-                const int ncolE = k ? c->opt.nstates : c->opt.nstates / 2;
+                const int ncolE = k ? c->nfilt : c->nfilt / 2;
                 group_var[k] = group_variant_f32(c, k == 1, ncolE);
             }
             for (Problem& P : c->probs) {
@@ -678,7 +688,9 @@ struct ScfRun {
     void filter_all() {
         const double ta = now_s();
         for (int p = 0; p < passes(); ++p) {
-            if (batched) {
+            if (tail64) {
+                for (Problem& P : c->probs) chefsi_pass(c, P, SDFT_FP64, P.X64);
+            } else if (batched) {
                 for (int k = 0; k < 2; ++k)
                     if (!groups[k].empty()) chefsi_pass_group(c, groups[k], group_var[k]);
                 for (Problem* P : single) chefsi_pass(c, *P, prec, P->X);
@@ -692,7 +704,7 @@ struct ScfRun {
     // occupations, density, energy, error, log; Pulay update unless finished.  Returns done.
     bool end_iteration() {
         fermi_device(c, c->probs[0].eig, c->probs[0].occ, c->scal + 8);
-        density_all(c, prec, false);
+        density_all(c, tail64 ? SDFT_FP64 : prec, tail64);
         E = energy_hf(c, c->rho_in, c->veff, c->exc, c->phi, etmp);
         SDFT_CUDA(cudaMemcpyAsync(diff, c->rho_out, sizeof(double) * nv, cudaMemcpyDeviceToDevice, c->stream));
         axpby_dev(c, diff, c->rho_in, -1.0, 1.0, nv);
@@ -725,6 +737,13 @@ struct ScfRun {
             done = true;
             return true;
         }
+        if (prec == SDFT_MIXED && c->opt.gemm_fp32_switch_tol > 0.0 && err < c->opt.gemm_fp32_switch_tol)
+            c->gemm_fp32 = true;   // FP32 CUDA-core Gram and rotation from the next pass on
+        if (!tail64 && prec == SDFT_MIXED && c->opt.fp64_switch_tol > 0.0 && err < c->opt.fp64_switch_tol) {
+            // the next passes continue from FP64 copies of the current orbitals
+            for (Problem& P : c->probs) convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, c->nfilt);
+            tail64 = true;
+        }
         if (it + 1 < c->opt.max_scf) pulay_update(c);
         ++it;
         done = it >= c->opt.max_scf;
@@ -734,10 +753,15 @@ struct ScfRun {
     sdft_status finish(sdft_result* out) {
         const sdft_status status = converged ? SDFT_OK : SDFT_ERR_NOT_CONVERGED;
         // final FP64 pass for the mixed path, at the last V_eff
-        bool have64 = prec == SDFT_FP64;
-        if (prec == SDFT_MIXED && c->opt.final_fp64_pass) {
+        c->gemm_fp32 = false;   // the step-level calls after the SCF use the tensor cores again
+        bool have64 = prec == SDFT_FP64 || tail64;
+        if (tail64) {
+            // keep the mixed-storage orbitals current for a following run (molecular dynamics)
+            for (Problem& P : c->probs) convert_block(c, P.cplx, SDFT_FP64, P.X64, P.X, c->nfilt);
+        }
+        if (prec == SDFT_MIXED && c->opt.final_fp64_pass && !tail64) {
             for (Problem& P : c->probs) {
-                convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, c->opt.nstates);
+                convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, c->nfilt);
                 chefsi_pass(c, P, SDFT_FP64, P.X64);
             }
             fermi_device(c, c->probs[0].eig, c->probs[0].occ, c->scal + 8);
@@ -784,7 +808,7 @@ struct ScfRun {
         c->mu = E.mu;
         c->ts = E.ts;
         if (!have64)
-            for (Problem& P : c->probs) convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, ns);
+            for (Problem& P : c->probs) convert_block(c, P.cplx, SDFT_MIXED, P.X, P.X64, c->nfilt);
         forces_compute(c);
         push_scf_history(c);
         resolve_timing(c);
@@ -830,7 +854,8 @@ sdft_status run_batch_scf(const std::vector<sdft_ctx*>& ctxs, sdft_result* out) 
     for (auto& r : runs) r->begin();
     auto multi_ok = [&](const ScfRun& r) {
         const sdft_ctx* c = r.c;
-        return r.prec == SDFT_MIXED && c->probs.size() == 1 && !c->probs[0].cplx && c->stream == ctxs[0]->stream;
+        return r.prec == SDFT_MIXED && !r.tail64 && c->probs.size() == 1 && !c->probs[0].cplx &&
+               c->stream == ctxs[0]->stream;
     };
     for (;;) {
         std::vector<ScfRun*> live;

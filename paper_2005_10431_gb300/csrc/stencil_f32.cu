@@ -148,10 +148,10 @@ void launch_multi_step_f32(const std::vector<sdft_ctx*>& ctxs, std::vector<Multi
         P.tiles_x = (c->n[0] + TX - 1) / TX;
         P.tiles_y = (c->n[1] + TY - 1) / TY;
         P.cta_begin = (int)total;
-        total += (long long)P.tiles_x * P.tiles_y * (c->opt.nstates / 2) * P.A.nzc;
+        total += (long long)P.tiles_x * P.tiles_y * (c->nfilt / 2) * P.A.nzc;
         P.cta_end = (int)total;
         max_natom = std::max(max_natom, c->natom);
-        bytes += (double)(c->opt.nstates / 2) * (double)c->ng * sizeof(float2) * (prev ? 3.0 : 2.0);
+        bytes += (double)(c->nfilt / 2) * (double)c->ng * sizeof(float2) * (prev ? 3.0 : 2.0);
     }
     SDFT_REQUIRE(total < (1LL << 31), SDFT_ERR_INVALID_ARG, "multi-cell launch too large");
     SDFT_CUDA(cudaMemcpyToSymbolAsync(c_multi, probs.data(), sizeof(MultiProblem) * n, 0, cudaMemcpyHostToDevice,
@@ -172,7 +172,7 @@ void launch_multi_step_f32(const std::vector<sdft_ctx*>& ctxs, std::vector<Multi
 // z chunks of one cell inside a multi-cell launch: at least 16 planes per chunk, enough CTAs overall
 int multi_nzc(const sdft_ctx* c, long long ctas_other) {
     const long long want = 8LL * 152;
-    const long long base = (long long)((c->n[0] + 31) / 32) * ((c->n[1] + 7) / 8) * (c->opt.nstates / 2);
+    const long long base = (long long)((c->n[0] + 31) / 32) * ((c->n[1] + 7) / 8) * (c->nfilt / 2);
     int nzc = 1;
     while (ctas_other + base * nzc < want && c->n[2] / (nzc + 1) >= 16) ++nzc;
     return nzc;
@@ -205,7 +205,7 @@ void chebyshev_filter_multi(const std::vector<sdft_ctx*>& ctxs, const std::vecto
         SDFT_REQUIRE(got == 2, SDFT_ERR_INVALID_ARG, "no free block buffers for the filter");
         ring[i] = {t[0], t[1], (float2*)Y[i]};
         nzc[i] = multi_nzc(c, ctas);
-        ctas += (long long)((c->n[0] + 31) / 32) * ((c->n[1] + 7) / 8) * (c->opt.nstates / 2) * nzc[i];
+        ctas += (long long)((c->n[0] + 31) / 32) * ((c->n[1] + 7) / 8) * (c->nfilt / 2) * nzc[i];
     }
     auto slot = [&](int i, int k) -> float2* { return ring[i][(((2 - (m - k)) % 3) + 3) % 3]; };
     // KB projections of every (step, cell): one table, uploaded once, one grouped launch per step
@@ -218,7 +218,7 @@ void chebyshev_filter_multi(const std::vector<sdft_ctx*>& ctxs, const std::vecto
         if (kb.S == 0 || kb.natom == 0) continue;
         kcell.push_back(i);
         max_natom = std::max(max_natom, kb.natom);
-        max_ncolE = std::max(max_ncolE, ctxs[i]->opt.nstates / 2);
+        max_ncolE = std::max(max_ncolE, ctxs[i]->nfilt / 2);
     }
     const int nk = (int)kcell.size();
     if (nk > 0) {
@@ -229,7 +229,7 @@ void chebyshev_filter_multi(const std::vector<sdft_ctx*>& ctxs, const std::vecto
                 const KBTables& kb = c->kb[0];
                 const float2* cur = k == 1 ? (const float2*)X[i] : slot(i, k - 1);
                 ktab.push_back(KBProblem{cur, c->C32, kb.cnt, kb.idx, kb.val32, kb.gamma, kb.cap, kb.natom,
-                                         c->opt.nstates / 2, c->ng});
+                                         c->nfilt / 2, c->ng});
             }
         if (c0->m_ktab_cap < (int)ktab.size()) {
             c0->m_ktab = (KBProblem*)ctx_alloc(c0, sizeof(KBProblem) * ktab.size());

@@ -500,6 +500,16 @@ void block_map(CUtensorMap* m, const sdft_ctx* c, const float2* base, int ncolE,
 
 }  // namespace
 
+// tiled tensor map with a chosen swizzle (the tensor-core GEMMs' copies)
+void tma_encode_tiled(CUtensorMap* m, CUtensorMapDataType t, int rank, const void* base, const cuuint64_t* dims,
+                      const cuuint64_t* strides_bytes, const cuuint32_t* box, CUtensorMapSwizzle sw) {
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    const CUresult r = encode_fn()(m, t, (cuuint32_t)rank, const_cast<void*>(base), dims, strides_bytes, box, es,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    SDFT_REQUIRE(r == CUDA_SUCCESS, SDFT_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+}
+
 // row of the variant table: usable when the grid's n1 is the template's, TY divides n2 with at
 // least two slabs, the block is real FP32 and the KB table has at most S slots per point
 template <int N1, int TY, int NP, int S, int D>

@@ -71,3 +71,21 @@ def test_graph_replay_of_the_grouped_filter_is_exact(sd):
     assert eg == ed
     assert np.array_equal(sd.sdft_get_density(cg), sd.sdft_get_density(cd))
     assert lg == ld      # replayed graph launches are counted like direct ones
+
+
+def test_batched_chefsi_with_buffer_states_matches_oracle(sd):
+    # buffer states change the filtered block width (grouped launches, batched eigensolve over
+    # nstates + nbuffer) but not the fixed point: the oracle's occupied eigenvalues and energy hold
+    cell = workloads.kspin_small_cell()
+    ref = _gold("kspin_20")
+    ctx = sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species,
+                         dict(nstates=cell.nstates, nbuffer=4, cheb_degree=cell.cheb_degree, precision=sd.SDFT_MIXED,
+                              scf_tol=1e-6, max_scf=200, nspin=cell.nspin, kT=cell.kT, seed=cell.seed,
+                              batch_problems=1),
+                         kpts=cell.kpts, kw=cell.kw)
+    r = sd.sdft_scf(ctx)
+    assert r["converged"]
+    assert abs(r["energy"] - ref["energy"]) / cell.natom < 1e-5
+    e = sd.sdft_get_eigenvalues(ctx)
+    assert e.shape == (cell.nspin, len(cell.kpts), cell.nstates)
+    assert np.max(np.abs(e[:, :, :3] - np.array(ref["eigs"])[:, :, :3])) < 1e-5

@@ -249,15 +249,21 @@ def test_subspace_matrices_and_rotation_mixed(sd):
     assert _relerr(sd.unpack_block(x, 1, False), ref) < 1e-5
 
 
-@pytest.mark.parametrize("n", [(9, 10, 11), (9, 11, 13), (40, 40, 40)])
-def test_gram_tcgen05_bf16x3_matches_fp64(sd, n):
-    # 154 orbitals (two 128-row tiles, three tile pairs): the tensor-core BF16x3 path.  The split
-    # product drops lo*lo and the bf16 remainders: ~2^-16 relative per product, far less after
-    # summation; 2e-5 of sqrt(M_ii M_jj) is the bar.
-    cell = workloads.small_cell(npts=10, L=4.0, natom=2, seed=5, nstates=154)
+# (orbitals, grid): 154 = two 128-row tiles with a ragged 26-row one; 40 = one narrow tile; 258 and
+# 520 = three and five tiles (the rotation in two and three 144/176-column blocks); grids with a
+# ragged last 32-point stage and 128-point tile; an odd point count (no TMA copies of the paired
+# layout: the CUDA-core path) must give the same result
+GEMM_CASES = [(154, (9, 10, 11)), (154, (9, 11, 14)), (154, (40, 40, 40)), (40, (9, 10, 11)),
+              (258, (9, 10, 11)), (520, (12, 12, 10)), (154, (9, 11, 13))]
+
+
+@pytest.mark.parametrize("ns,n", GEMM_CASES)
+def test_gram_tcgen05_bf16x3_matches_fp64(sd, ns, n):
+    # The tensor-core BF16x3 path.  The split product drops lo*lo and the bf16 remainders: ~2^-16
+    # relative per product, far less after summation; 2e-5 of sqrt(M_ii M_jj) is the bar.
+    cell = workloads.small_cell(npts=10, L=4.0, natom=2, seed=5, nstates=ns)
     cell.n = n
     cell.L = tuple(0.4 * x for x in n)
-    ns = 154
     ng = int(np.prod(n))
     ctx = _ctx(sd, cell, sd.SDFT_MIXED, ns)
     rng = np.random.default_rng(17)
@@ -274,14 +280,13 @@ def test_gram_tcgen05_bf16x3_matches_fp64(sd, n):
     assert np.max(np.abs(h.cpu().numpy().T - H_ref) / scale) < 2e-5
 
 
-@pytest.mark.parametrize("n", [(9, 10, 11), (9, 11, 13), (40, 40, 40)])
-def test_rotation_tcgen05_bf16x3_matches_fp64(sd, n):
-    # X = Y Q with 154 orbitals on the tensor cores (two 128-column tiles, three K tiles, a
-    # ragged last grid tile): BF16x3 of FP32 operands, error ~2^-16 of |Y||Q| per term.
-    cell = workloads.small_cell(npts=10, L=4.0, natom=2, seed=5, nstates=154)
+@pytest.mark.parametrize("ns,n", GEMM_CASES)
+def test_rotation_tcgen05_bf16x3_matches_fp64(sd, ns, n):
+    # X = Y Q on the tensor cores (32-orbital K stages with a ragged last one, a ragged last grid
+    # tile): BF16x3 of FP32 operands, error ~2^-16 of |Y||Q| per term.
+    cell = workloads.small_cell(npts=10, L=4.0, natom=2, seed=5, nstates=ns)
     cell.n = n
     cell.L = tuple(0.4 * x for x in n)
-    ns = 154
     ng = int(np.prod(n))
     ctx = _ctx(sd, cell, sd.SDFT_MIXED, ns)
     rng = np.random.default_rng(23)
