@@ -680,8 +680,9 @@ def probe_pass(args):
            "pass_ms": best, "kernels": fam, "peaks": pk,
            "note": "one filter of the given degree + Rayleigh-Ritz (H.Y, Gram, generalized eigensolve, rotation); "
                    "kernel times from the library's per-family CUDA-event timers, the pass time from events "
-                   "around it; the eigensolve at this size runs on " + ("cuSOLVER sygvd" if ns > 160 else
-                                                                       "the library's own solver")}
+                   "around it; the eigensolve at this size runs " + (
+                       "as a one-CTA FP32 solve refined in FP64" if ns <= 160
+                       else "as cuSOLVER's FP32 sygvd refined in FP64 (Ogita-Aishima)")}
     if args.oracle_pass:
         out["oracle_pass"] = oracle_pass_estimate(cell, degree)
     print(json.dumps(out), flush=True)

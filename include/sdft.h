@@ -313,9 +313,10 @@ sdft_status sdft_subspace_matrices_noalloc(int precision, int is_complex, const 
  * column-major ncol x ncol device matrices (double2 for is_complex).  M must be positive definite.
  * On return Hs holds Q (Q^H M Q = I, eigenvector j in column j), eig (device, ncol) ascending; M is
  * overwritten (scratch).  ncol <= 64 uses the library's one-CTA Cholesky + Jacobi solver (unless
- * SDFT_EIGEN=0 selects cuSOLVER); a real problem with 64 < ncol <= 160 on an SDFT_MIXED context
- * uses an FP32 solve refined to FP64 accuracy (Ogita-Aishima steps + Rayleigh-Ritz inside
- * clusters of near-degenerate eigenvalues), accepted only if its FP64 residual and M-orthonormality
+ * SDFT_EIGEN=0 selects cuSOLVER); a real problem with 64 < ncol <= 1024 on an SDFT_MIXED context
+ * uses an FP32 solve (one CTA up to 160, cuSOLVER's FP32 sygvd above) refined to FP64 accuracy
+ * (Ogita-Aishima steps + Rayleigh-Ritz inside clusters of near-degenerate eigenvalues), accepted
+ * only if its FP64 residual and M-orthonormality
  * defect are below 1e-10 relative, else redone by cuSOLVER (SDFT_EIGEN=2 forces it on any context
  * and reports a rejection as an error instead); otherwise cuSOLVER sygvd/hegvd.  All after diagonal
  * equilibration.  SDFT_ERR_CHOLESKY if M is not positive definite. */
@@ -382,14 +383,15 @@ sdft_status sdft_get_stencil_variant(const sdft_ctx* ctx, int is_complex, int* i
 
 /* ---- tracing: per-kernel-family device time (paper Sec. 2.1 ".out ... various timings") -- */
 enum {
-    SDFT_K_STENCIL = 0,    /* fused H Y + Chebyshev step (bytes: Y, Yprev read + Ynext write) */
+    SDFT_K_STENCIL = 0,    /* fused H Y + Chebyshev step, FP32 blocks (bytes: Y, Yprev read + Ynext write) */
     SDFT_K_KB_PROJECT = 1, /* KB projection C = beta^H Y */
     SDFT_K_GRAM = 2,       /* M = Y^H Y, Hs = Y^H HY (flops: 4 ngrid ncol^2, complex x4) */
     SDFT_K_EIGEN = 3,      /* equilibration + generalized eigensolve */
     SDFT_K_ROTATE = 4,     /* X = Y Q (flops: 2 ngrid ncol^2, complex x4) */
     SDFT_K_POISSON = 5,    /* AAR Poisson solve (whole solve) */
     SDFT_K_DENSITY = 6,    /* density from orbitals */
-    SDFT_K_COUNT = 7
+    SDFT_K_STENCIL64 = 7,  /* the same step on FP64 blocks (FP64 path, final FP64 pass, Lanczos) */
+    SDFT_K_COUNT = 8
 };
 typedef struct {
     uint64_t launches;     /* timed launches (or solves) */

@@ -78,7 +78,7 @@ class sdft_kernel_stats(C.Structure):
 
 
 SDFT_K_STENCIL, SDFT_K_KB_PROJECT, SDFT_K_GRAM, SDFT_K_EIGEN, SDFT_K_ROTATE, SDFT_K_POISSON, SDFT_K_DENSITY = range(7)
-KERNEL_FAMILIES = ["stencil", "kb_project", "gram", "eigen", "rotate", "poisson", "density"]
+KERNEL_FAMILIES = ["stencil", "kb_project", "gram", "eigen", "rotate", "poisson", "density", "stencil_fp64"]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

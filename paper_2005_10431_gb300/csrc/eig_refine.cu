@@ -1,6 +1,7 @@
 // Subspace generalized eigensolve Hs q = lambda M q of Rayleigh-Ritz (paper Sec. 2.1, the
-// projected problem of CheFSI) for real blocks of 64 < n <= 160: an FP32 solve in one CTA,
-// refined to FP64 accuracy by FP64 matrix products that spread over the whole GPU.
+// projected problem of CheFSI) for real blocks of 64 < n <= 1024: an FP32 solve (one CTA for
+// n <= 160, cuSOLVER's FP32 sygvd above, where two n x n FP32 matrices no longer fit in one CTA's
+// shared memory), refined to FP64 accuracy by FP64 matrix products that spread over the GPU.
 //
 // The GB300's FP64 pipes are few, so a one-CTA FP64 reduction to tridiagonal form is slow for
 // these sizes (cuSOLVER's sygvd takes ~6.6 ms at n = 154).  This solver
@@ -31,7 +32,8 @@
 namespace sdft {
 namespace {
 
-constexpr int RE_MAX_N = 160;
+constexpr int RE_MAX_N = 160;        // one-CTA FP32 solve (step 1)
+constexpr int RE2_MAX_N = 1024;      // refinement (steps 2-3), FP32 start from cuSOLVER above RE_MAX_N
 constexpr int RE_KMAX = 32;          // largest cluster solved by step 3
 constexpr int RE_MAX_SWEEPS = 20;    // FP32 Jacobi
 constexpr int RE_CL_SWEEPS = 40;     // FP64 cluster Jacobi
@@ -309,8 +311,8 @@ __global__ void __launch_bounds__(1024, 1)
 refine_step_kernel(const double* __restrict__ G, const double* __restrict__ S, double* __restrict__ Tm,
                    double* __restrict__ eig, double* __restrict__ ws, int n, int step, int mode,
                    int* __restrict__ status, double* __restrict__ diag) {
-    __shared__ double lam[RE_MAX_N];
-    __shared__ int ord[RE_MAX_N], rnk[RE_MAX_N], first[RE_MAX_N], cstart[RE_MAX_N], csize[RE_MAX_N];
+    __shared__ double lam[RE2_MAX_N];
+    __shared__ int ord[RE2_MAX_N], rnk[RE2_MAX_N], first[RE2_MAX_N], cstart[RE2_MAX_N], csize[RE2_MAX_N];
     __shared__ unsigned long long s_eta, s_scale, s_inter, s_orth;
     __shared__ int s_bad;
     if (*status & ST_CHOLESKY) return;
@@ -471,20 +473,45 @@ refine_step_kernel(const double* __restrict__ G, const double* __restrict__ S, d
     }
 }
 
+// FP32 start for n > RE_MAX_N: d = diag(M)^-1/2, M32 = D M D, H32 = D Hs D (FP32, column-major)
+__global__ void equil32_kernel(const double* __restrict__ M, const double* __restrict__ Hs, int n,
+                               double* __restrict__ d, float* __restrict__ M32, float* __restrict__ H32) {
+    const long long nn = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        const double s = rsqrt(M[i + (long long)i * n]) * rsqrt(M[j + (long long)j * n]);
+        M32[e] = (float)(s * M[e]);
+        H32[e] = (float)(s * Hs[e]);
+        if (j == 0) d[i] = rsqrt(M[i + (long long)i * n]);
+    }
+}
+// X = D V in FP64 from cuSOLVER's FP32 eigenvectors (ascending); status = Cholesky failure or 0
+__global__ void start32_kernel(const float* __restrict__ V, const double* __restrict__ d, int n,
+                               const int* __restrict__ info, double* __restrict__ X, int* __restrict__ status) {
+    const long long nn = (long long)n * n;
+    const bool bad = *info != 0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x)
+        X[e] = d[e % n] * (double)V[e];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *status = bad ? ST_CHOLESKY : 0;
+}
+
 }  // namespace
 
-bool refined_eig_supported(int n) { return n >= 2 && n <= RE_MAX_N; }
+bool refined_eig_supported(int n) { return n >= 2 && n <= RE2_MAX_N; }
 
 bool refined_generalized_eig(sdft_ctx* c, const double* M, const double* Hs, double* Q, double* eig, int n) {
-    SDFT_REQUIRE(refined_eig_supported(n), SDFT_ERR_INVALID_ARG, "refined eigensolver supports 2 <= n <= 160");
+    SDFT_REQUIRE(refined_eig_supported(n), SDFT_ERR_INVALID_ARG, "refined eigensolver supports 2 <= n <= 1024");
     const size_t nn = (size_t)n * n;
-    if (!c->reig_buf) {
-        const size_t N2 = (size_t)RE_MAX_N * RE_MAX_N;
-        // X, X', T, P1, P2, G, S (FP64 n x n each), ws, eig, diag; L (FP32); status
-        c->reig_buf = (double*)ctx_alloc(c, sizeof(double) * (7 * N2 + 2 * RE_KMAX * RE_MAX_N + RE_MAX_N + 16) +
-                                                sizeof(float) * N2 + 16);
+    // scratch sized for the context's widest Rayleigh-Ritz block (at least RE_MAX_N)
+    const int nmax = std::max(RE_MAX_N, std::max(n, c->nfilt));
+    if (!c->reig_buf || c->reig_nmax < nmax) {
+        const size_t N2 = (size_t)nmax * nmax;
+        // X, X', T, P1, P2, G, S (FP64 n x n each), ws, eig, diag, d; L / M32 / H32 (FP32); status, info
+        c->reig_buf = (double*)ctx_alloc(c, sizeof(double) * (7 * N2 + 2 * RE_KMAX * nmax + 2 * nmax + 16) +
+                                                sizeof(float) * (3 * N2 + nmax) + 64);
+        c->reig_nmax = nmax;
     }
-    const size_t N2 = (size_t)RE_MAX_N * RE_MAX_N;
+    const size_t N2 = (size_t)c->reig_nmax * c->reig_nmax;
     double* X = c->reig_buf;
     double* Xn = X + N2;
     double* Tm = Xn + N2;
@@ -493,14 +520,41 @@ bool refined_generalized_eig(sdft_ctx* c, const double* M, const double* Hs, dou
     double* G = P2 + N2;
     double* S = G + N2;
     double* ws = S + N2;
-    double* ev = ws + 2 * RE_KMAX * RE_MAX_N;
-    double* diag = ev + RE_MAX_N;
+    double* ev = ws + 2 * RE_KMAX * (size_t)c->reig_nmax;
+    double* dsc = ev + c->reig_nmax;
+    double* diag = dsc + c->reig_nmax;
     float* Lg = reinterpret_cast<float*>(diag + 16);
-    int* status = reinterpret_cast<int*>(Lg + N2);
+    float* M32 = Lg + N2;
+    float* H32 = M32 + N2;
+    float* w32 = H32 + N2;
+    int* status = reinterpret_cast<int*>(w32 + c->reig_nmax);
+    int* info = status + 1;
     ScopedTimer timer(c, SDFT_K_EIGEN);
-    const size_t sm = eig32_smem(n);
-    SDFT_CUDA(cudaFuncSetAttribute(eig32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    eig32_kernel<<<1, 1024, sm, c->stream>>>(M, Hs, n, X, Lg, status);
+    if (n <= RE_MAX_N) {
+        const size_t sm = eig32_smem(n);
+        SDFT_CUDA(cudaFuncSetAttribute(eig32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        eig32_kernel<<<1, 1024, sm, c->stream>>>(M, Hs, n, X, Lg, status);
+    } else {
+        // FP32 generalized eigensolve by cuSOLVER on the equilibrated problem (workspace on first use)
+        if (c->reig_lwork32 < 0 || c->reig_work32_n < n) {
+            int lw = 0;
+            cusolverStatus_t cs = cusolverDnSsygvd_bufferSize(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                                              CUBLAS_FILL_MODE_UPPER, n, H32, n, M32, n, w32, &lw);
+            SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "FP32 sygvd workspace query failed");
+            c->reig_work32 = (float*)ctx_alloc(c, sizeof(float) * ((size_t)lw + 64));
+            c->reig_lwork32 = lw;
+            c->reig_work32_n = n;
+        }
+        const unsigned g = (unsigned)std::min<size_t>((nn + 255) / 256, 152 * 8);
+        equil32_kernel<<<g, 256, 0, c->stream>>>(M, Hs, n, dsc, M32, H32);
+        SDFT_CUDA(cudaGetLastError());
+        const cusolverStatus_t cs = cusolverDnSsygvd(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                                     CUBLAS_FILL_MODE_UPPER, n, H32, n, M32, n, w32, c->reig_work32,
+                                                     c->reig_lwork32, info);
+        SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "FP32 sygvd failed to launch");
+        start32_kernel<<<g, 256, 0, c->stream>>>(H32, dsc, n, info, X, status);
+        SDFT_CUDA(cudaGetLastError());
+    }
     const dim3 grid((n + 31) / 32, (n + 31) / 32, 2);
     for (int step = 0; step < 3; ++step) {
         gemm64_kernel<false><<<grid, 256, 0, c->stream>>>(Prod2{{M, Hs}, {X, X}, {P1, P2}}, n, status);

@@ -148,6 +148,9 @@ struct sdft_ctx {
                                   //     n <= 160, else sygvd/hegvd; 0: sygvd/hegvd; 1: sygvj (real);
                                   //  2: FP32 + refinement wherever it applies, without fallback
     double* reig_buf = nullptr;   // scratch of the refined eigensolver (allocated on first use)
+    int reig_nmax = 0;            // the largest n that scratch holds
+    float* reig_work32 = nullptr; // cuSOLVER FP32 sygvd workspace (refined solve above n = 160)
+    int reig_lwork32 = -1, reig_work32_n = 0;
     int reig_last_status = 0;     // its last status word (0 = accepted)
     int reig_fallbacks = 0;       // refined solves rejected and redone by cuSOLVER
     int reig_accepted = 0;        // refined solves accepted

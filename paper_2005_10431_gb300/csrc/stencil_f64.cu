@@ -57,7 +57,7 @@ void launch_cheb_step<double>(sdft_ctx* c, int kpt, const double* Y, const doubl
         StepArgs<double> A = make_args<double>(c, kpt, alpha, beta, shift, c->n[2], 1);
         const long long total = (long long)ncolE * c->ng;
         const unsigned nb = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 32);
-        ScopedTimer timer(c, SDFT_K_STENCIL, (double)ncolE * (double)c->ng * sizeof(double) * (Yprev ? 3.0 : 2.0));
+        ScopedTimer timer(c, SDFT_K_STENCIL64, (double)ncolE * (double)c->ng * sizeof(double) * (Yprev ? 3.0 : 2.0));
         cheb_step_dirichlet_kernel<<<nb, 256, 0, c->stream>>>(Y, Yprev, Ynext, V, kb.S > 0 ? kbC : nullptr, kb.patom,
                                                              kb.pval64, kb.S, c->natom, ncolE, A);
         SDFT_CUDA(cudaGetLastError());

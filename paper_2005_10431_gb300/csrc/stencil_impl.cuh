@@ -838,7 +838,7 @@ void launch_variant(sdft_ctx* c, int kpt, const E* Y, const E* Yprev, E* Ynext, 
     const size_t dsm = sizeof(Stage<E, S, KV, TX, TY, 3>) * D +
                        (haskb_dsm(kbC, kb) ? sizeof(E) * (size_t)std::max(1, c->natom) : 0);
     const bool prev = Yprev != nullptr, hasv = V != nullptr, haskb = kbC != nullptr && kb.S > 0;
-    ScopedTimer timer(timed ? c : nullptr, SDFT_K_STENCIL,
+    ScopedTimer timer(timed ? c : nullptr, sizeof(S) == 8 ? SDFT_K_STENCIL64 : SDFT_K_STENCIL,
                       (double)ncolE * (double)c->ng * sizeof(E) * (prev ? 3.0 : 2.0));
 #define SDFT_STEP(P, K, VV, KN)                                                                      \
     do {                                                                                             \

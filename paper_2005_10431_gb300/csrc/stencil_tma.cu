@@ -510,14 +510,47 @@ void tma_encode_tiled(CUtensorMap* m, CUtensorMapDataType t, int rank, const voi
     SDFT_REQUIRE(r == CUDA_SUCCESS, SDFT_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
+int sm_count() {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        SDFT_CUDA(cudaGetDevice(&dev));
+        SDFT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return nsm;
+}
+
+// the persistent schedule of a slab launch (see launch_slab_variant): CTAs per slab, units per CTA,
+// and the largest number of pair groups one CTA's run of units spans (its KB coefficients are staged)
+struct SlabSchedule {
+    int nper, per_cta, gmax;
+};
+SlabSchedule slab_schedule(const sdft_ctx* c, int ncolE, int NP, int TY, int MINB) {
+    const int nslab = c->n[1] / TY, ngrp = (ncolE + NP - 1) / NP;
+    const int total = ngrp * c->n[2];
+    SlabSchedule s;
+    s.nper = std::max(1, std::min(sm_count() * MINB / nslab, total));
+    s.per_cta = (total + s.nper - 1) / s.nper;
+    s.gmax = 1;
+    for (int k = 0; k < s.nper; ++k) {
+        const int f0 = k * s.per_cta, f1 = std::min(total, f0 + s.per_cta);
+        if (f0 >= f1) break;
+        s.gmax = std::max(s.gmax, (f1 - 1) / c->n[2] - f0 / c->n[2] + 1);
+    }
+    return s;
+}
+
 // row of the variant table: usable when the grid's n1 is the template's, TY divides n2 with at
-// least two slabs, the block is real FP32 and the KB table has at most S slots per point
+// least two slabs, the block is real FP32, the KB table has at most S slots per point, and the
+// stages plus the KB coefficients of the pair groups of one CTA's run fit in shared memory (every
+// slab variant is instantiated with one CTA per SM)
 template <int N1, int TY, int NP, int S, int D>
 bool slab_variant_ok(const sdft_ctx* c, int ncolE) {
     if (c->n[0] != N1 || c->n[1] % TY || c->n[1] < 2 * TY || TY < R || ncolE <= 0) return false;
     for (const KBTables& kb : c->kb)
         if (kb.cplx || kb.S > S) return false;
-    return slab_smem_bytes<N1, TY, NP, S, D>(c->natom) <= 227 * 1024;
+    const SlabSchedule sch = slab_schedule(c, ncolE, NP, TY, 1);
+    return slab_smem_bytes<N1, TY, NP, S, D>(c->natom, sch.gmax) <= 227 * 1024;
 }
 
 template <int N1, int TY, int NP, int RY, int S, int D, int MINB>
@@ -529,13 +562,6 @@ void launch_slab_variant(sdft_ctx* c, int kpt, const float2* Y, const float2* Yp
     const KBTables& kb = c->kb[kpt];
     const bool prev = Yprev != nullptr, haskb = kbC != nullptr && kb.S > 0;
     const int nslab = c->n[1] / TY, ngrp = (ncolE + NP - 1) / NP;
-    // persistent schedule: one CTA per resident slot, each taking an equal run of (item, plane) units
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        SDFT_CUDA(cudaGetDevice(&dev));
-        SDFT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    }
     SDFT_REQUIRE((long long)nslab * ngrp * c->n[2] < (1LL << 30) && (long long)ncolE * c->ng < (1LL << 31),
                  SDFT_ERR_INVALID_ARG, "slab stencil: block too large for 32-bit offsets");
     // every slab gets the same number of CTAs, which take equal runs of its (pair group, plane) units in
@@ -543,15 +569,9 @@ void launch_slab_variant(sdft_ctx* c, int kpt, const float2* Y, const float2* Yp
     // same time, so the y-halo rows one slab reads are the interior rows its neighbour has just pulled
     // into L2 (a few SMs may stay idle so that the counts are equal)
     const int total = ngrp * c->n[2];
-    const int nper = std::max(1, std::min(nsm * MINB / nslab, total));
+    const SlabSchedule sch = slab_schedule(c, ncolE, NP, TY, MINB);
+    const int nper = sch.nper, per_cta = sch.per_cta, gmax = sch.gmax;
     const int nblk = nper * nslab;
-    const int per_cta = (total + nper - 1) / nper;
-    int gmax = 1;
-    for (int k = 0; k < nper; ++k) {
-        const int f0 = k * per_cta, f1 = std::min(total, f0 + per_cta);
-        if (f0 >= f1) break;
-        gmax = std::max(gmax, (f1 - 1) / c->n[2] - f0 / c->n[2] + 1);
-    }
     const size_t dsm = slab_smem_bytes<N1, TY, NP, S, D>(c->natom, gmax);
     SDFT_REQUIRE(dsm <= 227 * 1024, SDFT_ERR_INVALID_ARG,
                  "slab stencil: KB coefficients of the CTA's pair groups do not fit in shared memory");

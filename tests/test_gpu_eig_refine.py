@@ -1,6 +1,6 @@
-"""The refined subspace eigensolver (real, 64 < n <= 160): an FP32 Cholesky + Jacobi solve in one
-CTA, two FP64 Ogita-Aishima refinement steps and an FP64 Rayleigh-Ritz inside clusters of
-(near-)degenerate eigenvalues.  SDFT_EIGEN=2 forces it and turns a rejected result into an error
+"""The refined subspace eigensolver (real, 64 < n <= 1024): an FP32 Cholesky + Jacobi solve in one
+CTA (n <= 160; cuSOLVER's FP32 sygvd above), two FP64 Ogita-Aishima refinement steps and an FP64
+Rayleigh-Ritz inside clusters of (near-)degenerate eigenvalues.  SDFT_EIGEN=2 forces it and turns a rejected result into an error
 instead of the cuSOLVER fallback, so these tests see the refined path itself."""
 import numpy as np
 import pytest
@@ -60,7 +60,7 @@ def _solve(sd, n, H, M):
     return out
 
 
-@pytest.mark.parametrize("n", [65, 100, 154, 160])
+@pytest.mark.parametrize("n", [65, 100, 154, 160, 180, 300])
 def test_refined_eig_matches_lapack(sd, n, monkeypatch):
     import scipy.linalg as sla
     monkeypatch.setenv("SDFT_EIGEN", "2")
