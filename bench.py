@@ -383,11 +383,13 @@ def run_ours(args, rank, world, dist):
         pass
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     hits, niters, energies, converged = [], [], [], []
+    pits = []
     with ClockSampler(uuid) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
             r, log = one_step()
             hits.append(hit_time(log, e_ref, cell.natom))
+            pits = [rec.get("poisson_iters", 0) for rec in log]
             niters.append(r["niter"])
             energies.append(r["energy"])
             converged.append(bool(r["converged"]))
@@ -481,7 +483,9 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "scf": {"niter": niters, "energy": energies, "oracle_energy": e_ref if g else None, "converged": converged,
-                "hit_s": hits, "dE_per_atom": [abs(e - e_ref) / cell.natom for e in energies] if g else None},
+                "hit_s": hits, "dE_per_atom": [abs(e - e_ref) / cell.natom for e in energies] if g else None,
+                "poisson_aar_iters_per_solve": (sum(pits) / len(pits)) if pits else None,
+                "poisson_aar_iters_max": max(pits) if pits else None},
         "kernel_seconds": {k: v["seconds"] for k, v in stats.items()},
         "fp64_gpu": fp64,
         "learned_guess": learned,

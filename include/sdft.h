@@ -152,6 +152,9 @@ typedef struct {
     double mu;         /* Fermi level */
     double seconds;    /* device time (CUDA events) from the start of sdft_scf to the end of this iteration */
     double lower, cutoff, upper; /* filter bounds a0, a, b of the first problem */
+    int poisson_iters;  /* AAR iterations of this iteration's Poisson solve (FP32 correction
+                           iterations summed over the refinement rounds on the mixed path) */
+    double poisson_tol; /* the relative residual that solve was asked for */
 } sdft_iter_record;
 
 typedef struct {

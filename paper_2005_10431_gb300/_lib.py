@@ -63,7 +63,8 @@ class sdft_options(C.Structure):
 
 class sdft_iter_record(C.Structure):
     _fields_ = [("iter", C.c_int), ("energy", C.c_double), ("scf_error", C.c_double), ("mu", C.c_double),
-                ("seconds", C.c_double), ("lower", C.c_double), ("cutoff", C.c_double), ("upper", C.c_double)]
+                ("seconds", C.c_double), ("lower", C.c_double), ("cutoff", C.c_double), ("upper", C.c_double),
+                ("poisson_iters", C.c_int), ("poisson_tol", C.c_double)]
 
 
 class sdft_result(C.Structure):

@@ -603,6 +603,8 @@ struct ScfRun {
     bool converged = false, done = false;
     double last_err = 1.0;
     int it = 0, niter = 0;
+    int last_pit = 0;          // AAR iterations and requested tolerance of the last Poisson solve
+    double last_ptol = 0.0;
     Energies E{};
     // batched CheFSI: problems of one storage kind that a grouped row-tile launch fits
     std::vector<Problem*> groups[2], single;
@@ -670,6 +672,8 @@ struct ScfRun {
         const int pit = prec == SDFT_MIXED ? poisson_mixed(c, ftmp, c->phi, ptol, 4000)
                                            : poisson_aar(c, ftmp, c->phi, ptol, 4000);
         if (pit < 0) throw Error{SDFT_ERR_NOT_CONVERGED, "Poisson AAR did not converge"};
+        last_pit = pit;
+        last_ptol = ptol;
         veff_assemble(c);
         SDFT_CUDA(cudaStreamSynchronize(c->stream));
         t_pois += now_s() - ta;
@@ -730,6 +734,8 @@ struct ScfRun {
         rec.lower = c->probs[0].lower;
         rec.cutoff = c->probs[0].cutoff;
         rec.upper = c->probs[0].upper;
+        rec.poisson_iters = last_pit;
+        rec.poisson_tol = last_ptol;
         c->log.push_back(rec);
         niter = it + 1;
         if (err < c->opt.scf_tol) {
