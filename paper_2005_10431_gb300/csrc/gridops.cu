@@ -1347,33 +1347,56 @@ __global__ void __launch_bounds__(AAR_BS) aar_persistent_kernel(AarPersistArgs A
         float* xc = cur ? A.x1 : A.x0;
         float* xn = cur ? A.x0 : A.x1;
         const int slot = head;
-        // residual and history push on own points
-        for (long long g = lo + threadIdx.x; g < hi; g += blockDim.x) {
-            const int i = (int)(g % A.n1), j = (int)((g / A.n1) % A.n2), k = (int)(g / plane);
-            float acc = (float)A.K.c0 * xc[g];
+        // residual and history push on own points.  Grid coordinates advance incrementally in
+        // 32-bit arithmetic (the points of a thread are blockDim apart), so no division per point.
+        {
+            const int n1 = A.n1, n2 = A.n2, n3 = A.n3;
+            const int pl32 = n1 * n2;
+            int g = (int)lo + (int)threadIdx.x;
+            int i = g % n1, row = g / n1;
+            int j = row % n2, k = row / n2;
+            const int di = (int)(blockDim.x % (unsigned)n1), drow = (int)(blockDim.x / (unsigned)n1);
+            const int dj = drow % n2, dk = drow / n2;
+            for (; g < (int)hi; g += (int)blockDim.x) {
+                const int rowbase = g - i;              // (k n2 + j) n1
+                const int colbase = g - j * n1;         // k n1 n2 + i
+                const int plbase = g - k * pl32;        // j n1 + i
+                float acc = (float)A.K.c0 * xc[g];
 #pragma unroll
-            for (int rr = 1; rr <= FD_RADIUS; ++rr) {
-                int ip = i + rr, im = i - rr, jp = j + rr, jm = j - rr, kp = k + rr, km = k - rr;
-                ip -= ip >= A.n1 ? A.n1 : 0;
-                im += im < 0 ? A.n1 : 0;
-                jp -= jp >= A.n2 ? A.n2 : 0;
-                jm += jm < 0 ? A.n2 : 0;
-                kp -= kp >= A.n3 ? A.n3 : 0;
-                km += km < 0 ? A.n3 : 0;
-                const long long row = g - i, col = g - (long long)j * A.n1, pl = g - k * plane;
-                acc += (float)A.K.c[0][rr] * (xc[row + ip] + xc[row + im]);
-                acc += (float)A.K.c[1][rr] * (xc[col + (long long)jp * A.n1] + xc[col + (long long)jm * A.n1]);
-                acc += (float)A.K.c[2][rr] * (xc[pl + kp * plane] + xc[pl + km * plane]);
+                for (int rr = 1; rr <= FD_RADIUS; ++rr) {
+                    int ip = i + rr, im = i - rr, jp = j + rr, jm = j - rr, kp = k + rr, km = k - rr;
+                    ip -= ip >= n1 ? n1 : 0;
+                    im += im < 0 ? n1 : 0;
+                    jp -= jp >= n2 ? n2 : 0;
+                    jm += jm < 0 ? n2 : 0;
+                    kp -= kp >= n3 ? n3 : 0;
+                    km += km < 0 ? n3 : 0;
+                    acc += (float)A.K.c[0][rr] * (xc[rowbase + ip] + xc[rowbase + im]);
+                    acc += (float)A.K.c[1][rr] * (xc[colbase + jp * n1] + xc[colbase + jm * n1]);
+                    acc += (float)A.K.c[2][rr] * (xc[plbase + kp * pl32] + xc[plbase + km * pl32]);
+                }
+                const float r = A.b[g] - 2.f * acc;
+                A.r[g] = r;
+                const float fi = A.cj * r;
+                if (it > 0) {
+                    A.Xs[(long long)slot * A.n + g] = xc[g] - A.xprev[g];
+                    A.Fs[(long long)slot * A.n + g] = fi - A.fprev[g];
+                }
+                A.xprev[g] = xc[g];
+                A.fprev[g] = fi;
+                // next point of this thread: blockDim further along x, then y, then z
+                i += di;
+                j += dj;
+                k += dk;
+                if (i >= n1) {
+                    i -= n1;
+                    ++j;
+                }
+                if (j >= n2) {
+                    j -= n2;
+                    ++k;
+                }
             }
-            const float r = A.b[g] - 2.f * acc;
-            A.r[g] = r;
-            const float fi = A.cj * r;
-            if (it > 0) {
-                A.Xs[(long long)slot * A.n + g] = xc[g] - A.xprev[g];
-                A.Fs[(long long)slot * A.n + g] = fi - A.fprev[g];
-            }
-            A.xprev[g] = xc[g];
-            A.fprev[g] = fi;
         }
         if (it > 0) {
             head = (head + 1) % AAR_M;
@@ -1481,8 +1504,9 @@ static int aar_fp32_persistent(sdft_ctx* c, const float* b, float* x, double tol
         c->aar_persistent = false;
         return aar_fp32(c, b, x, tol_rel, max_iter, final_rel);
     }
-    // one CTA per SM (fewer arrivals per barrier, even work), fewer for small grids
-    long long nblk = std::min<long long>((long long)nsm, (n + 1023) / 1024);
+    // every co-resident CTA (latency hiding for the stencil's scattered loads), fewer for small grids
+    SDFT_REQUIRE(n < (1LL << 31) - 4096, SDFT_ERR_INVALID_ARG, "persistent Poisson solver: grid too large");
+    long long nblk = std::min<long long>((long long)nsm * per_sm, (n + 1023) / 1024);
     nblk = std::max<long long>(1, std::min<long long>(nblk, 12288 / AAR_ND));
     A.expected_blocks = (unsigned)nblk + (c->test_barrier_extra ? 1u : 0u);
     if (c->test_barrier_extra) A.spin_limit = 200000;
