@@ -102,3 +102,21 @@ def test_batch_scf_rejects_repeated_context(sd):
         sd.sdft_batch_scf([ctx, ctx])
     assert e.value.code == -1
     sd.sdft_destroy(ctx)
+
+
+def test_batch_scf_of_uneven_cells_converges_with_buffer_states(sd):
+    """The uneven cells of the batching workload reach the density tolerance 1e-6 within 100 SCF
+    iterations in the lockstep batch when their filtered blocks carry buffer states and the last
+    iterations take FP32 Rayleigh-Ritz GEMMs (without them several cells stop at the cap)."""
+    cells = workloads.uneven_cells(count=8, seed=3)
+    stream = torch.cuda.Stream()
+    ctxs = [sd.sdft_create(c.L, c.n, c.pos, c.types, c.species,
+                           dict(nstates=c.nstates, nbuffer=4, cheb_degree=c.cheb_degree, precision=sd.SDFT_MIXED,
+                                scf_tol=1e-6, max_scf=100, kT=c.kT, seed=c.seed, gemm_fp32_switch_tol=4e-6),
+                           stream=stream) for c in cells]
+    rs = sd.sdft_batch_scf(ctxs)
+    assert all(r["converged"] for r in rs), [r["niter"] for r in rs]
+    for ctx, c in zip(ctxs, cells):
+        rho = sd.sdft_get_density(ctx)
+        assert abs(float(np.prod(c.h)) * rho.sum() - c.nelec) < 1e-8 * c.nelec
+        sd.sdft_destroy(ctx)
