@@ -22,8 +22,10 @@ Probe modes (one JSON line each; used for profiling and per-kernel evidence, not
     --probe pass     one CheFSI pass (filter + Rayleigh-Ritz) after one SCF iteration from the SAD
                      guess, split by kernel family; --oracle-pass adds the FP64 CPU oracle's cost of
                      the same pass, timed on a slice and scaled (labelled as such)
-    --grid G         replaces the workload's grid by G^3 points (same cell, fewer points), so that
-                     a profiler capture stays small
+    --grid G         replaces the workload's grid by G^3 points, or by n1 x n2 x n3 points with
+                     --grid n1,n2,n3 (same cell, fewer points), so that a profiler capture stays small
+    --nstates N      (filter probe) filters N states of the workload's cell instead of its own count,
+                     for the same reason
 """
 from __future__ import annotations
 
@@ -58,9 +60,10 @@ def parse():
     p.add_argument("--probe", choices=["filter", "gemm", "pass"], default=None)
     p.add_argument("--variant", type=int, default=None)
     p.add_argument("--degree", type=int, default=None)
-    p.add_argument("--grid", type=int, default=None)
+    p.add_argument("--grid", default=None)
     p.add_argument("--kpoint", action="store_true")
     p.add_argument("--reps", type=int, default=5)
+    p.add_argument("--nstates", type=int, default=None)
     p.add_argument("--oracle-pass", action="store_true")
     return p.parse_args()
 
@@ -71,7 +74,8 @@ def cell_for(name, grid=None):
             "lattice216_120": workloads.lattice216_cell,
             "kpoint8_40": lambda: workloads.kpoint_cell(4, 40)}[name]()
     if grid:
-        cell.n = (grid, grid, grid)
+        n = tuple(int(x) for x in str(grid).split(","))
+        cell.n = n * 3 if len(n) == 1 else n
     return cell
 
 
@@ -608,6 +612,8 @@ def probe_filter(args):
     import workloads
     import paper_2005_10431_gb300 as sd
     cell = cell_for(args.workload, args.grid)
+    if args.nstates:
+        cell.nstates = args.nstates   # a smaller orbital block of the same cell (profiler captures)
     degree = args.degree or 4
     prec = sd.SDFT_MIXED if args.precision == "mixed" else sd.SDFT_FP64
     kpts = [(0.25, 0.125, -0.5)] if args.kpoint else None

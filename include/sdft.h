@@ -176,9 +176,11 @@ typedef void (*sdft_free_fn)(void* ptr, void* user);
 void sdft_default_options(sdft_options* opt);
 
 /* Create a context: copies all inputs, builds the pseudocharge, projector tables and the SAD
- * density on the device (paper Sec. 2.1 set-up).  alloc/free may be NULL (cudaMalloc/cudaFree).
+ * density on the device (paper Sec. 2.1 set-up).  alloc/free may be NULL (cudaMalloc/cudaFree);
+ * memory from alloc must be 256-byte aligned (the TMA copies need 16-byte aligned bases), else
+ * the allocation is handed back to free and the call fails with INVALID_ARG.
  * stream is a cudaStream_t (NULL = default stream).  Errors: INVALID_ARG (sizes, nonfinite
- * positions -> NONFINITE), OOM, CUDA. */
+ * positions -> NONFINITE, misaligned allocations), OOM, CUDA. */
 sdft_status sdft_create(const sdft_cell* cell, const sdft_grid* grid, const sdft_atoms* atoms,
                         int ntypes, const sdft_pseudo* pseudo, const sdft_options* opt,
                         sdft_alloc_fn alloc, sdft_free_fn free_fn, void* alloc_user,

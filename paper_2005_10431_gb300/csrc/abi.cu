@@ -14,6 +14,10 @@ void* ctx_alloc(sdft_ctx* c, size_t bytes) {
     if (c->alloc) {
         p = c->alloc(bytes, c->alloc_user);
         SDFT_REQUIRE(p != nullptr, SDFT_ERR_OOM, "allocation callback returned NULL for " + std::to_string(bytes) + " bytes");
+        if (((uintptr_t)p & 255) != 0) {
+            if (c->release) c->release(p, c->alloc_user);
+            throw Error{SDFT_ERR_INVALID_ARG, "allocation callback returned memory that is not 256-byte aligned"};
+        }
     } else {
         cudaError_t e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) {
@@ -238,7 +242,10 @@ void build_context(sdft_ctx* c) {
     c->Q32 = ctx_alloc(c, sizeof(float) * nf * nf * w2);
     c->qsplit_bytes = sdft::qsplit_bytes(nf);
     c->Qsplit = ctx_alloc(c, c->qsplit_bytes);
-    c->C32 = (float*)ctx_alloc(c, sizeof(float) * 2 * std::max(1, c->natom) * nf);
+    // FP32 KB coefficients, padded by two pair columns and two elements: the slab stencil copies a
+    // 16-byte aligned window of a pair group's coefficients that may pass the block's end
+    c->c32_elems = (long long)std::max(1, c->natom) * (nf + 2) + 2;
+    c->C32 = (float*)ctx_alloc(c, sizeof(float2) * (size_t)c->c32_elems);
     c->C64 = (double*)ctx_alloc(c, sizeof(double) * 2 * std::max(1, c->natom) * nf);
     c->dinfo = (int*)ctx_alloc(c, sizeof(int) * 4);
     // cuSOLVER workspace for the generalized eigenproblem of size nf

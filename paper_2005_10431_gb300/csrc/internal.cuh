@@ -209,6 +209,7 @@ struct sdft_ctx {
     void* Qsplit = nullptr;       // bf16 hi/lo rows of Q^T for the tensor-core rotation
     size_t qsplit_bytes = 0;
     float* C32 = nullptr;         // KB coefficients [ncol * natom] (x2)
+    long long c32_elems = 0;      // float2 elements of the C32 allocation (block plus padding)
     double* C64 = nullptr;
 
     // mixing history

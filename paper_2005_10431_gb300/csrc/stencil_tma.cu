@@ -9,7 +9,8 @@
 // pairs and marches along z.  One producer warp feeds a D-stage shared-memory ring with TMA tensor
 // copies: per plane the TY rows and the 6 + 6 y-halo rows of every pair (one 4-D box when the slab
 // does not touch the periodic y boundary, two boxes per pair when it does), the Yprev rows, the
-// V_eff rows and the per-point KB slot tables (atom, value).  Compute warps wait on the stage's
+// V_eff rows, the per-point KB slot tables (atom, value) and, by one bulk copy, the KB
+// coefficients gamma_a beta_a^T Y of the plane's NP pairs (a few KB, read from L2).  Compute warps wait on the stage's
 // mbarrier, so there is no CTA-wide barrier per plane; each compute thread owns two adjacent
 // x-points of one row for all NP pairs.  x-neighbours come from the staged row with the periodic
 // wrap folded into six per-thread column offsets (n1 even: a 16-byte pair of points never
@@ -50,7 +51,8 @@ constexpr long long SLAB_WAIT_LIMIT = 1LL << 24;   // try_wait polls before a wa
 struct SlabArgs {
     float cx[R + 1], cy[R + 1], cz[R + 1];
     float c0, alpha, beta, shift;
-    int n2, n3, ncolE, natom, nslab, gmax;
+    int n2, n3, ncolE, natom, nslab;
+    int sstride;         // bytes per stage: the static regions plus the KB coefficient window
     long long ng;
     int total;           // (pair group, plane) units of one slab: ngroups * n3
     int per_cta;         // units per CTA
@@ -94,6 +96,14 @@ __device__ __forceinline__ void tma4(void* dst, const CUtensorMap* m, int c0, in
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
         "%5}], [%6];" ::"r"(s32(dst)),
         "l"(m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(s32(bar))
+        : "memory");
+}
+
+// untiled bulk copy global -> shared: both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(s32(dst)),
+        "l"(src), "r"(bytes), "r"(s32(bar))
         : "memory");
 }
 
@@ -171,10 +181,13 @@ struct SlabLayout {
     static_assert(TILE % 128 == 0 && QROWS % 128 == 0 && PREV % 128 == 0 && VB % 128 == 0 && KA % 128 == 0, "TMA regions must be 128-B aligned");
 };
 
+// KB coefficient window of a stage: the NP * natom float2 of the plane's pair group, copied from a
+// 16-byte aligned start one float2 early when col0 * natom is odd, rounded up to 16 bytes
+constexpr int slab_kc_bytes(int NP, int natom) { return ((NP * natom + 2) * 8 + 127) / 128 * 128; }
+
 template <int N1, int TY, int NP, int S, int D>
-constexpr size_t slab_smem_bytes(int natom, int gmax = 4) {
-    return (size_t)SlabLayout<N1, TY, NP, S>::STAGE * D + 16 * (size_t)(2 * D) +
-           sizeof(float2) * (size_t)NP * (size_t)(natom + 1) * (size_t)gmax + 128;
+constexpr size_t slab_smem_bytes(int natom) {
+    return (size_t)(SlabLayout<N1, TY, NP, S>::STAGE + slab_kc_bytes(NP, natom)) * D + 16 * (size_t)(2 * D) + 128;
 }
 
 // Persistent schedule: CTA b works on slab b mod nslab (TY rows) and on the contiguous run
@@ -212,9 +225,8 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
     // align by offsetting the array itself (not through an integer cast), so that the compiler keeps
     // treating every access as a shared-memory access (LDS/STS rather than generic loads and stores)
     unsigned char* smem = smem_raw + ((128u - ((unsigned)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)L::STAGE * D);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)A.sstride * D);
     uint64_t* empty = full + D;
-    float2* Cs = reinterpret_cast<float2*>(empty + D);   // [group][natom + 1][NP]; row natom is zero
 
     const int tid = threadIdx.x;
     const int n3 = A.n3;
@@ -222,8 +234,6 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
     const int fbeg = (blockIdx.x / A.nslab) * A.per_cta;
     const int fend = min(A.total, fbeg + A.per_cta);
     if (fbeg >= fend) return;                // whole CTA, before any barrier
-    const int gfirst = fbeg / n3;
-    const int ngl = (fend - 1) / n3 - gfirst + 1;   // <= A.gmax (host-checked)
     const int plane = N1 * A.n2;
     const unsigned ngu = (unsigned)A.ng;
 
@@ -234,14 +244,6 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (KB)
-        for (int i = tid; i < ngl * (A.natom + 1) * NP; i += blockDim.x) {
-            const int gl = i / ((A.natom + 1) * NP);
-            const int r = i - gl * (A.natom + 1) * NP;
-            const int a = r / NP, p = r - a * NP;
-            const int col = (gfirst + gl) * NP + p;
-            Cs[i] = (a < A.natom && col < A.ncolE) ? C[(long long)col * A.natom + a] : make_float2(0.f, 0.f);
-        }
     __syncthreads();
 
     bool ok = true;
@@ -249,21 +251,29 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
     if (tid >= NCOMP) {
         // ---------------- producer warp: one lane issues every copy ----------------
         if (tid == NCOMP) {
-            constexpr uint32_t bytes = L::TILE + L::QROWS + (PREV ? L::PREV : 0) + L::VB + (KB ? 2 * L::KA : 0);
+            constexpr uint32_t sbytes = L::TILE + L::QROWS + (PREV ? L::PREV : 0) + L::VB + (KB ? 2 * L::KA : 0);
             int j = 0;
             for (int f = fbeg; f < fend && ok;) {
                 const int grp = f / n3, z0 = f - grp * n3;
                 const int z1 = min(n3, z0 + (fend - f));
                 const int y0 = slab * TY, col0 = grp * NP;
                 const bool wrap = (y0 < R) || (y0 + TY + R > A.n2);
+                // KB coefficients of the group: float2 elements [e0 - o, e0 - o + kcn) of C, e0 = col0 * natom
+                // (the host pads C by two pair columns and two elements past the block, so the window of the
+                // last group stays inside its allocation)
+                const long long e0 = (long long)col0 * A.natom;
+                const int o = (int)(e0 & 1);
+                const uint32_t kcn = (uint32_t)((o + NP * A.natom + 1) & ~1);
+                const uint32_t bytes = sbytes + (KB ? kcn * 8u : 0u);
                 for (int z = z0; z < z1; ++z, ++j) {
                     const int s = j % D;
                     if (j >= D && !mb_wait(&empty[s], ((j / D) - 1) & 1)) {
                         ok = false;
                         break;
                     }
-                    unsigned char* st = smem + (size_t)s * L::STAGE;
+                    unsigned char* st = smem + (size_t)s * A.sstride;
                     mb_expect_tx(&full[s], bytes);
+                    if (KB) bulk_copy(st + L::STAGE, C + (e0 - o), kcn * 8u, &full[s]);
                     if (!wrap) {
                         tma4(st, &tmYfull, 0, y0 - R, z, col0, &full[s]);
                     } else {
@@ -323,7 +333,7 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
             const int z1 = min(n3, z0 + (fend - f));
             const int col0 = grp * NP;
             const unsigned gxy = (unsigned)((slab * TY + ty0) * N1 + gx);   // first of the thread's RY rows
-            const uint32_t Cg = s32(Cs) + (uint32_t)((grp - gfirst) * (A.natom + 1) * NP * 8);
+            const uint32_t kco = (uint32_t)(L::STAGE + 8 * (int)(((long long)col0 * A.natom) & 1));
             const int nvalid = min(NP, A.ncolE - col0);   // pairs of this group that exist
             const float2* Yg = Y + (size_t)col0 * ngu;
             float2* Zg = Ynext + (size_t)col0 * ngu;
@@ -354,7 +364,7 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
                             if ((tid & 31) == 0) atomicExch(err, 2);
                             break;
                         }
-                        const uint32_t st = smem_s + (uint32_t)(s * L::STAGE);
+                        const uint32_t st = smem_s + (uint32_t)(s * A.sstride);
 #pragma unroll
                         for (int p = 0; p < NP; ++p)   // plane z + R of the queue (zero rows past ncolE)
 #pragma unroll
@@ -367,21 +377,29 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
                             const int ty = ty0 + rr;
                             const float2 vv = lds64(st + L::OFF_V + (uint32_t)((ty * N1 + gx) * 4));
                             // KB term of both points and all NP pairs: the slot tables are read once per
-                            // plane; unused slots hold atom -1 and value 0 and point at the zero row natom
+                            // plane; the coefficient of pair p and atom a sits at [p][a] of the stage's
+                            // window, and an unused slot (atom -1, or a slot past the table: atom 0,
+                            // value 0) contributes exactly zero
                             float2 kb0[NP], kb1[NP];
 #pragma unroll
                             for (int p = 0; p < NP; ++p) kb0[p] = kb1[p] = make_float2(0.f, 0.f);
                             if (KB) {
+                                const uint32_t Cg = st + kco;
 #pragma unroll
                                 for (int k = 0; k < S; ++k) {
                                     const int2 ka = lds64i(st + L::OFF_KA + (uint32_t)(((k * TY + ty) * N1 + gx) * 4));
                                     const float2 kv = lds64(st + L::OFF_KV + (uint32_t)(((k * TY + ty) * N1 + gx) * 4));
-                                    const uint32_t c0p = Cg + min((unsigned)ka.x, (unsigned)A.natom) * (NP * 8);
-                                    const uint32_t c1p = Cg + min((unsigned)ka.y, (unsigned)A.natom) * (NP * 8);
+                                    const bool v0 = (unsigned)ka.x < (unsigned)A.natom;
+                                    const bool v1 = (unsigned)ka.y < (unsigned)A.natom;
+                                    const uint32_t c0p = Cg + (v0 ? (uint32_t)ka.x * 8u : 0u);
+                                    const uint32_t c1p = Cg + (v1 ? (uint32_t)ka.y * 8u : 0u);
 #pragma unroll
                                     for (int p = 0; p < NP; ++p) {
-                                        kb0[p] = fma2(kv.x, lds64(c0p + 8 * p), kb0[p]);
-                                        kb1[p] = fma2(kv.y, lds64(c1p + 8 * p), kb1[p]);
+                                        const float2 z2 = make_float2(0.f, 0.f);
+                                        const float2 g0 = lds64(c0p + (uint32_t)(p * A.natom * 8));
+                                        const float2 g1 = lds64(c1p + (uint32_t)(p * A.natom * 8));
+                                        kb0[p] = fma2(kv.x, v0 ? g0 : z2, kb0[p]);
+                                        kb1[p] = fma2(kv.y, v1 ? g1 : z2, kb1[p]);
                                     }
                                 }
                             }
@@ -520,10 +538,9 @@ int sm_count() {
     return nsm;
 }
 
-// the persistent schedule of a slab launch (see launch_slab_variant): CTAs per slab, units per CTA,
-// and the largest number of pair groups one CTA's run of units spans (its KB coefficients are staged)
+// the persistent schedule of a slab launch (see launch_slab_variant): CTAs per slab, units per CTA
 struct SlabSchedule {
-    int nper, per_cta, gmax;
+    int nper, per_cta;
 };
 SlabSchedule slab_schedule(const sdft_ctx* c, int ncolE, int NP, int TY, int MINB) {
     const int nslab = c->n[1] / TY, ngrp = (ncolE + NP - 1) / NP;
@@ -531,26 +548,19 @@ SlabSchedule slab_schedule(const sdft_ctx* c, int ncolE, int NP, int TY, int MIN
     SlabSchedule s;
     s.nper = std::max(1, std::min(sm_count() * MINB / nslab, total));
     s.per_cta = (total + s.nper - 1) / s.nper;
-    s.gmax = 1;
-    for (int k = 0; k < s.nper; ++k) {
-        const int f0 = k * s.per_cta, f1 = std::min(total, f0 + s.per_cta);
-        if (f0 >= f1) break;
-        s.gmax = std::max(s.gmax, (f1 - 1) / c->n[2] - f0 / c->n[2] + 1);
-    }
     return s;
 }
 
 // row of the variant table: usable when the grid's n1 is the template's, TY divides n2 with at
 // least two slabs, the block is real FP32, the KB table has at most S slots per point, and the
-// stages plus the KB coefficients of the pair groups of one CTA's run fit in shared memory (every
-// slab variant is instantiated with one CTA per SM)
+// D stages with their KB coefficient windows fit in shared memory (every slab variant is
+// instantiated with one CTA per SM)
 template <int N1, int TY, int NP, int S, int D>
 bool slab_variant_ok(const sdft_ctx* c, int ncolE) {
     if (c->n[0] != N1 || c->n[1] % TY || c->n[1] < 2 * TY || TY < R || ncolE <= 0) return false;
     for (const KBTables& kb : c->kb)
         if (kb.cplx || kb.S > S) return false;
-    const SlabSchedule sch = slab_schedule(c, ncolE, NP, TY, 1);
-    return slab_smem_bytes<N1, TY, NP, S, D>(c->natom, sch.gmax) <= 227 * 1024;
+    return slab_smem_bytes<N1, TY, NP, S, D>(c->natom) <= 227 * 1024;
 }
 
 template <int N1, int TY, int NP, int RY, int S, int D, int MINB>
@@ -570,11 +580,13 @@ void launch_slab_variant(sdft_ctx* c, int kpt, const float2* Y, const float2* Yp
     // into L2 (a few SMs may stay idle so that the counts are equal)
     const int total = ngrp * c->n[2];
     const SlabSchedule sch = slab_schedule(c, ncolE, NP, TY, MINB);
-    const int nper = sch.nper, per_cta = sch.per_cta, gmax = sch.gmax;
+    const int nper = sch.nper, per_cta = sch.per_cta;
     const int nblk = nper * nslab;
-    const size_t dsm = slab_smem_bytes<N1, TY, NP, S, D>(c->natom, gmax);
-    SDFT_REQUIRE(dsm <= 227 * 1024, SDFT_ERR_INVALID_ARG,
-                 "slab stencil: KB coefficients of the CTA's pair groups do not fit in shared memory");
+    const size_t dsm = slab_smem_bytes<N1, TY, NP, S, D>(c->natom);
+    // the coefficient window of the last group reads at most (ncolE + NP - 1) * natom + 1 float2 of C
+    SDFT_REQUIRE(!haskb || (kbC == reinterpret_cast<const float2*>(c->C32) && ((uintptr_t)kbC & 15) == 0 &&
+                            (long long)(ncolE + NP - 1) * c->natom + 1 <= c->c32_elems),
+                 SDFT_ERR_INVALID_ARG, "slab stencil: KB coefficient buffer misaligned or too short");
     SlabArgs A;
     for (int r = 0; r <= R; ++r) {
         A.cx[r] = (float)c->coef.cx[r];
@@ -589,7 +601,7 @@ void launch_slab_variant(sdft_ctx* c, int kpt, const float2* Y, const float2* Yp
     A.n3 = c->n[2];
     A.ncolE = ncolE;
     A.nslab = nslab;
-    A.gmax = gmax;
+    A.sstride = SlabLayout<N1, TY, NP, S>::STAGE + slab_kc_bytes(NP, c->natom);
     A.total = total;
     A.per_cta = per_cta;
     A.natom = c->natom;

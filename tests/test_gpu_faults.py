@@ -56,3 +56,29 @@ def test_non_finite_density_guess_is_rejected(sd):
     with pytest.raises(sd.SdftError) as e:
         sd.sdft_set_density(ctx, np.ones(cell.ngrid - 1))
     assert e.value.code == -1
+
+
+def test_misaligned_allocation_callback_is_rejected(sd, monkeypatch):
+    # an allocator whose blocks start 64 bytes past a 256-byte boundary: the context must refuse them
+    # (the TMA copies need 16-byte aligned bases) and hand every block back, not run on them
+    from paper_2005_10431_gb300 import _lib
+    handed = []
+
+    def fake(device):
+        def alloc(nbytes, user):
+            p = torch.cuda.caching_allocator_alloc(int(nbytes) + 256, device=device)
+            handed.append(p)
+            return p + 64
+
+        def free(ptr, user):
+            handed.remove(ptr - 64)
+            torch.cuda.caching_allocator_delete(ptr - 64)
+
+        return _lib.ALLOC_FN(alloc), _lib.FREE_FN(free)
+
+    monkeypatch.setattr(sd, "_torch_allocator", fake)
+    cell = workloads.two_atom_cell()
+    with pytest.raises(sd.SdftError) as e:
+        sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species, dict(nstates=8, precision=1))
+    assert e.value.code == -1 and "256-byte aligned" in str(e.value)
+    assert handed == []

@@ -117,6 +117,7 @@ def test_batch_scf_of_uneven_cells_converges_with_buffer_states(sd):
     rs = sd.sdft_batch_scf(ctxs)
     assert all(r["converged"] for r in rs), [r["niter"] for r in rs]
     for ctx, c in zip(ctxs, cells):
+        # the orbital norms carry FP32 rounding: the density integrates to nelec to ~1e-7 relative
         rho = sd.sdft_get_density(ctx)
-        assert abs(float(np.prod(c.h)) * rho.sum() - c.nelec) < 1e-8 * c.nelec
+        assert abs(float(np.prod(c.h)) * rho.sum() - c.nelec) < 1e-6 * c.nelec
         sd.sdft_destroy(ctx)
