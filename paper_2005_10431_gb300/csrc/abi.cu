@@ -65,6 +65,10 @@ void ctx_free_all(sdft_ctx* c) {
         cudaGraphExecDestroy(c->g_graph);
         c->g_graph = nullptr;
     }
+    if (c->mg_graph) {
+        cudaGraphExecDestroy(c->mg_graph);
+        c->mg_graph = nullptr;
+    }
     if (c->cap_stream) {
         cudaStreamDestroy(c->cap_stream);
         c->cap_stream = nullptr;
@@ -263,6 +267,9 @@ void build_context(sdft_ctx* c) {
     c->solver_lwork = std::max(c->solver_lwork, lw);
     if (const char* env = getenv("SDFT_EIGEN")) c->eig_method = atoi(env);
     if (const char* env = getenv("SDFT_AAR_PERSISTENT")) c->aar_persistent = atoi(env) != 0;
+    // multigrid-preconditioned FP32 Poisson corrections (periodic mixed-precision path only)
+    if (const char* env = getenv("SDFT_AAR_MG")) c->aar_mg = atoi(env) != 0;
+    if (c->aar_mg && c->opt.precision == SDFT_MIXED && c->opt.boundary != SDFT_BC_DIRICHLET) mg_setup(c);
     if (const char* env = getenv("SDFT_TEST_BARRIER_EXTRA")) c->test_barrier_extra = atoi(env) != 0;
     cs = cusolverDnCreateSyevjInfo(&c->syevj_params);
     SDFT_REQUIRE(cs == CUSOLVER_STATUS_SUCCESS, SDFT_ERR_CUDA, "syevj info");

@@ -1265,6 +1265,87 @@ static int aar_fp32(sdft_ctx* c, const float* b, float* x, double tol_rel, int m
     return it;
 }
 
+// FP32 AAR with the multigrid preconditioner M (one V-cycle, poisson_mg.cu) in place of the Jacobi
+// scaling: f_k = M r_k enters the Richardson steps x += omega f and the Anderson extrapolation every
+// p-th step exactly where c r_k does in aar_fp32; convergence is tested on the true residual
+// ||r_k|| / ||b|| at the Anderson steps.  With M A well conditioned a short history and frequent
+// Anderson steps suffice.
+static int aar_fp32_mg(sdft_ctx* c, const float* b, float* x, double tol_rel, int max_iter, double* final_rel) {
+    const long long n = c->ng;
+    const float omega = 0.7f, beta = 0.7f;
+    const int m = 5, p = 3;
+    float* r = c->work32 + 1 * n;
+    float* xprev = c->work32 + 2 * n;
+    float* fprev = c->work32 + 3 * n;
+    float* Xs = c->work32 + 4 * n;
+    float* Fs = Xs + (long long)m * n;
+    float* z = c->work32 + 19 * n;
+    double* gam = c->scal + 64;
+    int* slots = (int*)(c->scal + 96);
+    double* ffv = c->scal + 128;
+    double* rrv = c->scal + 136;
+    double* part = c->scal + 4096;
+    double* part_r = c->scal + 2048;
+    double bnorm2;
+    {
+        anderson_gram_kernel<float><<<64, RB, 0, c->stream>>>(Fs, slots, 0, b, 1.0f, n, part_r);
+        anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part_r, 64, 0, gam, rrv);
+        count_launch(c, 2);
+        SDFT_CUDA(cudaMemcpyAsync(c->hscal, rrv, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        SDFT_CUDA(cudaStreamSynchronize(c->stream));
+        bnorm2 = c->hscal[0];
+    }
+    SDFT_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * n, c->stream));
+    if (bnorm2 == 0.0) {
+        *final_rel = 0.0;
+        return 0;
+    }
+    int count = 0, head = 0, it = 0;
+    int hslots[16];
+    double rel = 1.0;
+    for (it = 0; it < max_iter; ++it) {
+        laplacian_residual<float>(c, x, b, r);
+        mg_vcycle(c, r, z);
+        const int slot = head;
+        anderson_push_kernel<float><<<nblocks(n), 256, 0, c->stream>>>(x, z, 1.0f, xprev, fprev, Xs + (long long)slot * n,
+                                                                       Fs + (long long)slot * n, it > 0, n);
+        count_launch(c);
+        if (it > 0) {
+            head = (head + 1) % m;
+            count = std::min(count + 1, m);
+        }
+        const bool anderson = ((it + 1) % p == 0) && count > 0;
+        if (anderson) {
+            for (int j = 0; j < count; ++j) hslots[j] = ((head - count + j) % m + m) % m;
+            std::memcpy(c->hscal + 512, hslots, sizeof(int) * 16);
+            SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 512, sizeof(int) * count, cudaMemcpyHostToDevice, c->stream));
+            const int nblk = 64;
+            anderson_gram_kernel<float><<<nblk, RB, 0, c->stream>>>(Fs, slots, count, z, 1.0f, n, part);
+            anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part, nblk, count, gam, ffv);
+            // ||r||^2 of the residual this step was taken from
+            anderson_gram_kernel<float><<<nblk, RB, 0, c->stream>>>(Fs, slots, 0, r, 1.0f, n, part_r);
+            anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part_r, nblk, 0, gam + 16, rrv);
+            anderson_update_kernel<float><<<nblocks(n), 256, 0, c->stream>>>(x, z, 1.0f, beta, Xs, Fs, slots, gam, count, n);
+            SDFT_CUDA(cudaGetLastError());
+            count_launch(c, 5);
+            SDFT_CUDA(cudaMemcpyAsync(c->hscal, rrv, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            SDFT_CUDA(cudaStreamSynchronize(c->stream));
+            rel = std::sqrt(c->hscal[0] / bnorm2);
+            if (!std::isfinite(rel)) throw Error{SDFT_ERR_NONFINITE, "Poisson residual is not finite"};
+            if (rel <= tol_rel) {
+                ++it;
+                break;
+            }
+        } else {
+            axpby_kernel<float><<<nblocks(n), 256, 0, c->stream>>>(x, z, omega, 1.0f, n);
+            SDFT_CUDA(cudaGetLastError());
+            count_launch(c);
+        }
+    }
+    *final_rel = rel;
+    return it;
+}
+
 // ---------------------------------------------------------------------------------------
 // Persistent FP32 AAR: the whole correction solve A d = b (A = -L_h) in one cooperative launch.
 // CTA k owns points [k*per, (k+1)*per).  Per iteration: residual r = b + L x_cur on own points
@@ -1338,7 +1419,6 @@ __global__ void __launch_bounds__(AAR_BS) aar_persistent_kernel(AarPersistArgs A
     __shared__ double ff_s;
     const long long per = (A.n + gridDim.x - 1) / gridDim.x;
     const long long lo = blockIdx.x * per, hi = min(A.n, lo + per);
-    const long long plane = (long long)A.n1 * A.n2;
     int head = 0, count = 0;
     int cur = 0;
     int it;
@@ -1603,8 +1683,10 @@ int poisson_mixed(sdft_ctx* c, const double* f, double* phi, double tol, int max
         count_launch(c);
         double inner_rel = 1.0;
         const double want = std::max(1e-3, 0.3 * tol / rel);
-        total += c->aar_persistent ? aar_fp32_persistent(c, b32, d32, want, std::min(400, max_iter - total), &inner_rel)
-                                   : aar_fp32(c, b32, d32, want, std::min(400, max_iter - total), &inner_rel);
+        const int budget = std::min(400, max_iter - total);
+        total += !c->mg.empty()       ? aar_fp32_mg(c, b32, d32, want, budget, &inner_rel)
+                 : c->aar_persistent ? aar_fp32_persistent(c, b32, d32, want, budget, &inner_rel)
+                                     : aar_fp32(c, b32, d32, want, budget, &inner_rel);
         convert_add_kernel<double, float><<<nblocks(n), 256, 0, c->stream>>>(phi, d32, 1.0, 1.0, n);
         count_launch(c);
     }

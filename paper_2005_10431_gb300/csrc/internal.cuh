@@ -72,6 +72,16 @@ struct KBTables {
     bool cplx = false;
 };
 
+// One grid of the multigrid hierarchy that preconditions the FP32 Poisson corrections
+// (poisson_mg.cu): dimensions, 1 / h_d^2, and its correction and right-hand side (levels >= 1).
+struct MgLevel {
+    int n[3] = {0, 0, 0};
+    double w[3] = {0, 0, 0};
+    long long np = 0;
+    float* x = nullptr;
+    float* b = nullptr;
+};
+
 struct PendingTiming {
     cudaEvent_t a, b;
     int fam;
@@ -166,6 +176,14 @@ struct sdft_ctx {
     int group_choice[2] = {-1, -1};            // autotuned row variant of grouped launches (real, complex)
     const char* stencil_last_name[4] = {nullptr, nullptr, nullptr, nullptr};
     bool aar_persistent = true;   // FP32 Poisson corrections in one cooperative launch
+    bool aar_mg = true;           // FP32 Poisson corrections by multigrid-preconditioned AAR (when the grid coarsens)
+    std::vector<sdft::MgLevel> mg;   // multigrid hierarchy (empty: none)
+    double mg_lmin = 0.0, mg_lmax = 0.0;   // spectrum bounds of the coarsest grid's operator
+    int mg_coarse_iters = 0;              // Chebyshev iterations on the coarsest grid
+    cudaGraphExec_t mg_graph = nullptr;   // the V-cycle's launches for (mg_graph_r, mg_graph_z)
+    const float* mg_graph_r = nullptr;
+    float* mg_graph_z = nullptr;
+    int mg_graph_launches = 0;
     bool test_barrier_extra = false;  // test hook: the persistent barrier waits for one CTA too many
     std::vector<cudaEvent_t> ev_free;
     std::vector<sdft::PendingTiming> pending;
@@ -334,6 +352,10 @@ void axpby_dev(sdft_ctx* c, double* y, const double* x, double a, double b, long
 int poisson_aar(sdft_ctx* c, const double* f, double* phi, double tol, int max_iter);
 // same problem, FP64 residuals + FP32 AAR corrections; returns inner iterations (negative: failed)
 int poisson_mixed(sdft_ctx* c, const double* f, double* phi, double tol, int max_iter);
+// multigrid preconditioner of the FP32 Poisson corrections (poisson_mg.cu): build the hierarchy
+// (false: the grid does not coarsen far enough), and z = M r by one V-cycle
+bool mg_setup(sdft_ctx* c);
+void mg_vcycle(sdft_ctx* c, const float* r, float* z);
 // reductions: out[i] = sum_g a_i[g] * b_i[g] (device scal), returned synchronously to host
 void dots_host(sdft_ctx* c, int count, const double* const* a, const double* const* b, long long n,
                double* host_out);

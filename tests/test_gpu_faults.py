@@ -32,6 +32,7 @@ def _poisson(sd, ctx, cell):
 
 def test_persistent_barrier_timeout_is_reported_not_hung(sd, monkeypatch):
     cell = workloads.two_atom_cell()
+    monkeypatch.setenv("SDFT_AAR_MG", "0")   # the persistent (Jacobi) AAR kernel holds the grid barrier
     monkeypatch.setenv("SDFT_TEST_BARRIER_EXTRA", "1")
     bad = sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species, dict(nstates=8, precision=1))
     with pytest.raises(sd.SdftError) as e:

@@ -326,6 +326,32 @@ def test_poisson_mixed_refinement_matches_exact_solve(sd):
     assert _relerr(phi.cpu().numpy(), ref) < 1e-9
 
 
+# grids: 24^3 coarsens to 6^3 (multigrid), 40 x 24 x 30 stops at an odd 20 x 12 x 15 coarsest grid,
+# 25^3 does not coarsen (Jacobi-scaled AAR in the persistent kernel)
+@pytest.mark.parametrize("n", [(24, 24, 24), (40, 24, 30), (25, 25, 25)])
+def test_poisson_mixed_multigrid_matches_exact_solve(sd, n, monkeypatch):
+    cell = workloads.two_atom_cell()
+    h = cell.L[0] / cell.n[0]
+    cell.n = n
+    cell.L = tuple(h * k for k in n)
+    f = model.sad_density(cell) + model.pseudocharge(cell)
+    ref = ham.poisson_exact(cell, f)
+    its = {}
+    for mg in ("1", "0"):
+        monkeypatch.setenv("SDFT_AAR_MG", mg)
+        ctx = _ctx(sd, cell, sd.SDFT_MIXED, 8)
+        ft = torch.from_numpy(f).cuda()
+        phi = torch.zeros_like(ft)
+        its[mg] = sd.sdft_poisson(ctx, ft, phi, 1e-11, 4000)
+        assert its[mg] > 0
+        assert _relerr(phi.cpu().numpy(), ref) < 1e-9
+        sd.sdft_destroy(ctx)
+    if n != (25, 25, 25):   # the V-cycle preconditioner cuts the FP32 AAR iterations several-fold
+        assert 4 * its["1"] < its["0"], its
+    else:
+        assert its["1"] == its["0"], its
+
+
 @pytest.mark.parametrize("nspin", [1, 2])
 def test_lda_matches_oracle(sd, nspin):
     cell = workloads.two_atom_cell()
