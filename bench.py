@@ -627,10 +627,19 @@ def probe_filter(args):
     sd.sdft_chebyshev_filter(ctx, 0, 0, prec, x, y, cell.nstates, degree, 5.0, 160.0, -1.0)
     torch.cuda.synchronize()
     st = sd.sdft_get_kernel_stats(ctx)["stencil"]
+    first_ms = 1e3 * st["seconds"]
+    # a second filter on the warm context: the timed one (the first includes the autotuner, module
+    # loading and first-touch costs)
+    sd.sdft_reset_kernel_stats(ctx)
+    sd.sdft_chebyshev_filter(ctx, 0, 0, prec, x, y, cell.nstates, degree, 5.0, 160.0, -1.0)
+    torch.cuda.synchronize()
+    st = sd.sdft_get_kernel_stats(ctx)["stencil"]
+    kb = sd.sdft_get_kernel_stats(ctx)["kb_project"]
     vidx, vname = sd.sdft_get_stencil_variant(ctx, args.kpoint)
     print(json.dumps({"probe": "filter", "workload": args.workload, "grid": list(cell.n), "nstates": cell.nstates,
                       "degree": degree, "variant": [vidx, vname], "stencil_launches": st["launches"],
-                      "stencil_ms": 1e3 * st["seconds"],
+                      "stencil_ms": 1e3 * st["seconds"], "first_call_stencil_ms": first_ms,
+                      "kb_project_ms": 1e3 * kb["seconds"], "kb_project_launches": kb["launches"],
                       "stencil_gbs": st["bytes"] / st["seconds"] / 1e9 if st["seconds"] > 0 else None}), flush=True)
 
 

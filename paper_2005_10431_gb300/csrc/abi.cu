@@ -250,6 +250,7 @@ void build_context(sdft_ctx* c) {
     // 16-byte aligned window of a pair group's coefficients that may pass the block's end
     c->c32_elems = (long long)std::max(1, c->natom) * (nf + 2) + 2;
     c->C32 = (float*)ctx_alloc(c, sizeof(float2) * (size_t)c->c32_elems);
+    c->C32b = (float*)ctx_alloc(c, sizeof(float2) * (size_t)c->c32_elems);
     c->C64 = (double*)ctx_alloc(c, sizeof(double) * 2 * std::max(1, c->natom) * nf);
     c->dinfo = (int*)ctx_alloc(c, sizeof(int) * 4);
     // cuSOLVER workspace for the generalized eigenproblem of size nf
@@ -269,6 +270,7 @@ void build_context(sdft_ctx* c) {
     if (const char* env = getenv("SDFT_AAR_PERSISTENT")) c->aar_persistent = atoi(env) != 0;
     // multigrid-preconditioned FP32 Poisson corrections (periodic mixed-precision path only)
     if (const char* env = getenv("SDFT_AAR_MG")) c->aar_mg = atoi(env) != 0;
+    if (const char* env = getenv("SDFT_FUSE_KB")) c->fuse_kb_projection = atoi(env) != 0;
     if (c->aar_mg && c->opt.precision == SDFT_MIXED && c->opt.boundary != SDFT_BC_DIRICHLET) mg_setup(c);
     if (const char* env = getenv("SDFT_TEST_BARRIER_EXTRA")) c->test_barrier_extra = atoi(env) != 0;
     cs = cusolverDnCreateSyevjInfo(&c->syevj_params);

@@ -1274,6 +1274,10 @@ static int aar_fp32_mg(sdft_ctx* c, const float* b, float* x, double tol_rel, in
     const long long n = c->ng;
     const float omega = 0.7f, beta = 0.7f;
     const int m = 5, p = 3;
+    // reduction grids: the history Gram's partials (m (m + 1) / 2 + m + 1 = 21 per block) fill at most
+    // 296 * 21 of the 12 288 doubles from scal + 4096; the single dot's fill 512 of the 1 024 from
+    // scal + 2048 (two blocks per SM: these are L2-resident vectors, latency-bound with fewer blocks)
+    constexpr int NB_G = 296, NB_R = 512;
     float* r = c->work32 + 1 * n;
     float* xprev = c->work32 + 2 * n;
     float* fprev = c->work32 + 3 * n;
@@ -1288,8 +1292,8 @@ static int aar_fp32_mg(sdft_ctx* c, const float* b, float* x, double tol_rel, in
     double* part_r = c->scal + 2048;
     double bnorm2;
     {
-        anderson_gram_kernel<float><<<64, RB, 0, c->stream>>>(Fs, slots, 0, b, 1.0f, n, part_r);
-        anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part_r, 64, 0, gam, rrv);
+        anderson_gram_kernel<float><<<NB_R, RB, 0, c->stream>>>(Fs, slots, 0, b, 1.0f, n, part_r);
+        anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part_r, NB_R, 0, gam, rrv);
         count_launch(c, 2);
         SDFT_CUDA(cudaMemcpyAsync(c->hscal, rrv, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         SDFT_CUDA(cudaStreamSynchronize(c->stream));
@@ -1319,12 +1323,11 @@ static int aar_fp32_mg(sdft_ctx* c, const float* b, float* x, double tol_rel, in
             for (int j = 0; j < count; ++j) hslots[j] = ((head - count + j) % m + m) % m;
             std::memcpy(c->hscal + 512, hslots, sizeof(int) * 16);
             SDFT_CUDA(cudaMemcpyAsync(slots, c->hscal + 512, sizeof(int) * count, cudaMemcpyHostToDevice, c->stream));
-            const int nblk = 64;
-            anderson_gram_kernel<float><<<nblk, RB, 0, c->stream>>>(Fs, slots, count, z, 1.0f, n, part);
-            anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part, nblk, count, gam, ffv);
+            anderson_gram_kernel<float><<<NB_G, RB, 0, c->stream>>>(Fs, slots, count, z, 1.0f, n, part);
+            anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part, NB_G, count, gam, ffv);
             // ||r||^2 of the residual this step was taken from
-            anderson_gram_kernel<float><<<nblk, RB, 0, c->stream>>>(Fs, slots, 0, r, 1.0f, n, part_r);
-            anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part_r, nblk, 0, gam + 16, rrv);
+            anderson_gram_kernel<float><<<NB_R, RB, 0, c->stream>>>(Fs, slots, 0, r, 1.0f, n, part_r);
+            anderson_solve_kernel<<<1, 256, 0, c->stream>>>(part_r, NB_R, 0, gam + 16, rrv);
             anderson_update_kernel<float><<<nblocks(n), 256, 0, c->stream>>>(x, z, 1.0f, beta, Xs, Fs, slots, gam, count, n);
             SDFT_CUDA(cudaGetLastError());
             count_launch(c, 5);

@@ -228,6 +228,11 @@ struct sdft_ctx {
     size_t qsplit_bytes = 0;
     float* C32 = nullptr;         // KB coefficients [ncol * natom] (x2)
     long long c32_elems = 0;      // float2 elements of the C32 allocation (block plus padding)
+    float* C32b = nullptr;        // second FP32 KB coefficient buffer (c32_elems float2): fused projections
+    float2* kb_next = nullptr;    // set around one FP32 step launch: where a slab step may also write the KB
+    bool kb_next_done = false;    //   coefficients of its output (kb_next_done: it did)
+    bool fuse_kb_projection = true;   // SDFT_FUSE_KB=0: always the separate projection pass
+    bool stencil_fuse = true;         // the autotuner's verdict: fused projection (where offered) faster
     double* C64 = nullptr;
 
     // mixing history

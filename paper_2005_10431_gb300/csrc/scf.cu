@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <type_traits>
 
 namespace sdft {
 
@@ -100,10 +101,17 @@ void filter_typed(sdft_ctx* c, int kpt, const E* X, E* Y, E* T1, E* T2, int ncol
     E* ring[3] = {T1, T2, Y};
     auto slot = [&](int k) -> E* { return ring[(((2 - (m - k)) % 3) + 3) % 3]; };
     const bool kb = c->kb[kpt].S > 0;
+    // FP32 real blocks: a slab-tile step may also produce the KB coefficients of its output (into the
+    // other coefficient buffer), which then replace the next step's projection pass
+    E* Cb[2] = {C, C};
+    if constexpr (std::is_same<E, float2>::value)
+        if (C == reinterpret_cast<E*>(c->C32) && !c->kb[kpt].cplx && c->fuse_kb_projection) Cb[1] = reinterpret_cast<E*>(c->C32b);
+    int ci = 0;
+    bool have = false;
     for (int k = 1; k <= m; ++k) {
         const E* cur = k == 1 ? X : slot(k - 1);
         const E* prev = k == 1 ? nullptr : (k == 2 ? X : slot(k - 2));
-        if (kb) launch_kb_project<E>(c, kpt, cur, C, ncolE);
+        if (kb && !have) launch_kb_project<E>(c, kpt, cur, Cb[ci], ncolE);
         double alpha, beta = 0.0;
         if (k == 1) {
             alpha = sigma1 / e;
@@ -113,7 +121,18 @@ void filter_typed(sdft_ctx* c, int kpt, const E* X, E* Y, E* T1, E* T2, int ncol
             beta = sigma * sigma2;
             sigma = sigma2;
         }
-        launch_cheb_step<E>(c, kpt, cur, prev, slot(k), ncolE, V, kb ? C : nullptr, alpha, beta, cc);
+        if constexpr (std::is_same<E, float2>::value) {
+            c->kb_next = (kb && k < m && Cb[1] != Cb[0]) ? reinterpret_cast<float2*>(Cb[ci ^ 1]) : nullptr;
+            c->kb_next_done = false;
+        }
+        launch_cheb_step<E>(c, kpt, cur, prev, slot(k), ncolE, V, kb ? Cb[ci] : nullptr, alpha, beta, cc);
+        have = false;
+        if constexpr (std::is_same<E, float2>::value) {
+            have = c->kb_next != nullptr && c->kb_next_done;
+            c->kb_next = nullptr;
+            c->kb_next_done = false;
+        }
+        if (have) ci ^= 1;
     }
 }
 

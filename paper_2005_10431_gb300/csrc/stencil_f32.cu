@@ -45,6 +45,11 @@ constexpr int kNCplx = sizeof(kCplx) / sizeof(kCplx[0]);
 }  // namespace
 
 template <>
+void launch_kb_project<float2>(sdft_ctx* c, int kpt, const float2* Y, float2* C, int ncolE) {
+    launch_project_impl<float2>(c, kpt, Y, C, ncolE);
+}
+
+template <>
 void launch_cheb_step<float2>(sdft_ctx* c, int kpt, const float2* Y, const float2* Yprev, float2* Ynext, int ncolE,
                               const float* V, const float2* kbC, double alpha, double beta, double shift,
                               bool with_kinetic) {
@@ -54,10 +59,23 @@ void launch_cheb_step<float2>(sdft_ctx* c, int kpt, const float2* Y, const float
     int& choice = c->stencil_choice[cplx ? 1 : 0];
     int pick = choice;
     if (pick < 0) {
-        pick = autotune_stencil<float2>(c, table, nvar, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift);
-        if (pick >= 0) choice = pick;   // small calls are not timed and do not fix the choice
-        else pick = 0;
+        // when the caller wants the output's KB coefficients too, the variants are timed with them (fused
+        // or by the separate pass, into the caller's target buffer, which the real launch then rewrites)
+        float2* kb_next = c->kb_next;
+        c->kb_next = nullptr;
+        bool fused = true;
+        pick = autotune_stencil<float2>(c, table, nvar, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift,
+                                        kb_next, kb_next ? &launch_kb_project<float2> : nullptr, &fused);
+        c->kb_next = kb_next;
+        if (pick >= 0) {   // small calls are not timed and do not fix the choice
+            choice = pick;
+            if (kb_next) c->stencil_fuse = fused;
+        } else {
+            pick = 0;
+        }
     }
+    if (!c->stencil_fuse) c->kb_next = nullptr;   // the separate projection pass was timed faster
+    c->kb_next_done = false;
     // the chosen variant may not fit this call (another column count): fall back to the column tile
     const int v = (table[pick].ok == nullptr || table[pick].ok(c, ncolE)) ? pick : 0;
     c->stencil_last[cplx ? 1 : 0] = v;
@@ -74,10 +92,6 @@ void launch_cheb_step<float>(sdft_ctx* c, int kpt, const float* Y, const float* 
                                                  with_kinetic, true);
 }
 
-template <>
-void launch_kb_project<float2>(sdft_ctx* c, int kpt, const float2* Y, float2* C, int ncolE) {
-    launch_project_impl<float2>(c, kpt, Y, C, ncolE);
-}
 
 // grouped FP32 launches: the row variant used is the autotuned one when it is a row tile that
 // fits, else the first row tile that fits; -1 if none does (callers then loop over problems)

@@ -707,7 +707,7 @@ cheb_row_kernel(const float2* __restrict__ Y_, const float2* __restrict__ Yprev_
 
 // KB projection: C[col][a] = gamma_a * sum_j conj(beta_a(j)) Y[idx_j, col], NC columns per CTA
 template <typename E, bool CPLX, int NC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 kb_project_kernel(const E* __restrict__ Y_, E* __restrict__ C_, const int* __restrict__ cnt_,
                   const int* __restrict__ idx_, const void* __restrict__ val_,
                   const double* __restrict__ gamma_, int cap_, int natom, int ncolE, long long ng,
@@ -741,9 +741,9 @@ kb_project_kernel(const E* __restrict__ Y_, E* __restrict__ C_, const int* __res
     E acc[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) acc[k] = ezero<E>();
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        const long long e = (long long)a * cap + j;
-        const int g = idx[e];
+    // two projector points per pass (2 NC independent gathers in flight per thread); the points of
+    // one thread are summed in the same order as one at a time
+    auto add_point = [&](long long e, int g) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             if (c0 + k < ncolE) {
@@ -757,7 +757,32 @@ kb_project_kernel(const E* __restrict__ Y_, E* __restrict__ C_, const int* __res
                 }
             }
         }
+    };
+    int j = threadIdx.x;
+    for (; j + (int)blockDim.x < m; j += 2 * blockDim.x) {
+        const long long e0 = (long long)a * cap + j, e1 = e0 + blockDim.x;
+        const int g0 = idx[e0], g1 = idx[e1];
+        E y0[NC], y1[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const bool in = c0 + k < ncolE;
+            y0[k] = in ? Y[(long long)(c0 + k) * ng + g0] : ezero<E>();
+            y1[k] = in ? Y[(long long)(c0 + k) * ng + g1] : ezero<E>();
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            if constexpr (CPLX) {
+                const E b0 = reinterpret_cast<const E*>(val)[e0], b1 = reinterpret_cast<const E*>(val)[e1];
+                acc[k] = eadd(acc[k], cmul_conj(b0, y0[k]));
+                acc[k] = eadd(acc[k], cmul_conj(b1, y1[k]));
+            } else {
+                const S b0 = reinterpret_cast<const S*>(val)[e0], b1 = reinterpret_cast<const S*>(val)[e1];
+                acc[k] = efma(b0, y0[k], acc[k]);
+                acc[k] = efma(b1, y1[k], acc[k]);
+            }
+        }
     }
+    if (j < m) add_point((long long)a * cap + j, idx[(long long)a * cap + j]);
     // block reduction (warp shuffles, then smem across warps)
     __shared__ E red[NC][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -956,9 +981,14 @@ struct StepVariant {
 // the chosen variant afterwards) and keep the fastest for this context.  SDFT_STENCIL_VARIANT=k
 // forces variant k.  Small problems use variant 0 without timing.
 template <typename E>
+// proj (not null): the caller also needs the KB coefficients of the step's output, so each variant is
+// timed with them: followed by the separate projection pass `project` into proj, and, where the
+// variant offers a fused projection (it then sets c->kb_next_done), also with that; *fused tells
+// which of the two the fastest variant used
 int autotune_stencil(sdft_ctx* c, const StepVariant<E>* table, int nvar, int kpt, const E* Y, const E* Yprev,
                      E* Ynext, int ncolE, const typename Elem<E>::S* V, const E* kbC, double alpha, double beta,
-                     double shift) {
+                     double shift, E* proj = nullptr,
+                     void (*project)(sdft_ctx*, int, const E*, E*, int) = nullptr, bool* fused = nullptr) {
     auto usable = [&](int v) { return table[v].ok == nullptr || table[v].ok(c, ncolE); };
     if (const char* env = getenv("SDFT_STENCIL_VARIANT")) {
         const int v = atoi(env);
@@ -970,21 +1000,42 @@ int autotune_stencil(sdft_ctx* c, const StepVariant<E>* table, int nvar, int kpt
     SDFT_CUDA(cudaEventCreate(&b));
     int best = 0;
     float best_ms = 1e30f;
+    // one step (and the output's projection when asked for); returns whether it was fused
+    auto run = [&](int v, bool fuse) {
+        if (proj != nullptr) {
+            c->kb_next = fuse ? reinterpret_cast<decltype(c->kb_next)>(proj) : nullptr;
+            c->kb_next_done = false;
+        }
+        table[v].fn(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, true, false);
+        bool done = false;
+        if (proj != nullptr) {
+            done = c->kb_next_done;
+            if (!done) project(c, kpt, Ynext, proj, ncolE);
+            c->kb_next = nullptr;
+            c->kb_next_done = false;
+        }
+        return done;
+    };
+    bool best_fused = false;
     for (int v = 0; v < nvar; ++v) {
         if (!usable(v)) continue;
-        table[v].fn(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, true, false);  // warm-up
-        SDFT_CUDA(cudaEventRecord(a, c->stream));
-        for (int r = 0; r < 3; ++r)
-            table[v].fn(c, kpt, Y, Yprev, Ynext, ncolE, V, kbC, alpha, beta, shift, true, false);
-        SDFT_CUDA(cudaEventRecord(b, c->stream));
-        SDFT_CUDA(cudaEventSynchronize(b));
-        float ms = 0.f;
-        SDFT_CUDA(cudaEventElapsedTime(&ms, a, b));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = v;
+        for (int fuse = 0; fuse < (proj != nullptr ? 2 : 1); ++fuse) {
+            const bool f = run(v, fuse != 0);   // warm-up
+            if (fuse && !f) break;              // no fused projection in this variant
+            SDFT_CUDA(cudaEventRecord(a, c->stream));
+            for (int r = 0; r < 3; ++r) run(v, fuse != 0);
+            SDFT_CUDA(cudaEventRecord(b, c->stream));
+            SDFT_CUDA(cudaEventSynchronize(b));
+            float ms = 0.f;
+            SDFT_CUDA(cudaEventElapsedTime(&ms, a, b));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = v;
+                best_fused = fuse != 0;
+            }
         }
     }
+    if (fused) *fused = best_fused;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     return best;
@@ -996,7 +1047,7 @@ template <typename E>
 void launch_project_group_impl(sdft_ctx* c, const KBProblem* grp, int nprob, int ncolE, bool cplx) {
     const int natom = c->natom;
     if (natom == 0 || ncolE == 0 || nprob == 0) return;
-    constexpr int NC = 4;
+    constexpr int NC = 8;
     dim3 grid(natom, (ncolE + NC - 1) / NC, nprob);
     ScopedTimer timer(c, SDFT_K_KB_PROJECT);
     if (cplx) {
@@ -1016,7 +1067,7 @@ void launch_project_group_impl(sdft_ctx* c, const KBProblem* grp, int nprob, int
 template <typename E>
 void launch_project_multi_impl(sdft_ctx* c, const KBProblem* grp, int nprob, int max_natom, int max_ncolE) {
     if (max_natom == 0 || max_ncolE == 0 || nprob == 0) return;
-    constexpr int NC = 4;
+    constexpr int NC = 8;
     dim3 grid(max_natom, (max_ncolE + NC - 1) / NC, nprob);
     ScopedTimer timer(c, SDFT_K_KB_PROJECT);
     kb_project_kernel<E, false, NC><<<grid, 256, 0, c->stream>>>(nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
@@ -1029,7 +1080,7 @@ template <typename E>
 void launch_project_impl(sdft_ctx* c, int kpt, const E* Y, E* C, int ncolE) {
     const KBTables& kb = c->kb[kpt];
     if (kb.natom == 0 || ncolE == 0) return;
-    constexpr int NC = 4;
+    constexpr int NC = 8;
     dim3 grid(kb.natom, (ncolE + NC - 1) / NC);
     ScopedTimer timer(c, SDFT_K_KB_PROJECT);
     using S = typename Elem<E>::S;

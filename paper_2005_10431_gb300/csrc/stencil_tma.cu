@@ -99,6 +99,11 @@ __device__ __forceinline__ void tma4(void* dst, const CUtensorMap* m, int c0, in
         : "memory");
 }
 
+// global float2 reduction (vector red, sm_90 and later)
+__device__ __forceinline__ void red_add2(float2* p, float2 v) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
+
 // untiled bulk copy global -> shared: both addresses 16-byte aligned, bytes a multiple of 16
 __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
@@ -206,9 +211,17 @@ constexpr int slab_maxreg() {
     return r > 255 ? 255 : r;
 }
 
-template <int N1, int TY, int NP, int RY, int S, int D, int MINB, bool PREV, bool KB>
+// PROJ (with KB, RY = 1): the step also accumulates the KB coefficients of its output,
+// Cn[col][a] += sum_points beta_a(point) Ynext[point][col] (Cn zeroed before, scaled by gamma_a after,
+// by the host), which the next step would otherwise compute by a separate pass over Ynext.  Each thread keeps, per KB slot,
+// the atom that slot held on the previous plane and a running sum for it (the slot's atom changes
+// only where the z-line of the thread's two points enters or leaves a projector sphere) and adds the
+// sum into Cn with one vector reduction when the atom changes and at the end of a pair group; the
+// second point of a slot whose atom differs from the first point's is added at once.
+template <int N1, int TY, int NP, int RY, int S, int D, int MINB, bool PREV, bool KB, bool PROJ>
 __global__ void __maxnreg__((slab_maxreg<N1, TY, RY, MINB>()))
 cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const float2* __restrict__ C,
+                 float2* __restrict__ Cn,
                  const __grid_constant__ CUtensorMap tmYfull, const __grid_constant__ CUtensorMap tmY6,
                  const __grid_constant__ CUtensorMap tmYmid, const __grid_constant__ CUtensorMap tmP,
                  const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmKA,
@@ -220,6 +233,7 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
     constexpr int NCW = NCOMP / 32;          // compute warps
     constexpr int QN = 2 * R + 1;            // register queue length (plane z + R arrives with stage z)
     static_assert(TY % RY == 0, "RY must divide TY");
+    static_assert(!PROJ || (KB && RY == 1), "the fused projection needs the KB term and one row per thread");
     static_assert(NCOMP % 32 == 0, "compute threads must fill whole warps");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // align by offsetting the array itself (not through an integer cast), so that the compiler keeps
@@ -337,6 +351,26 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
             const int nvalid = min(NP, A.ncolE - col0);   // pairs of this group that exist
             const float2* Yg = Y + (size_t)col0 * ngu;
             float2* Zg = Ynext + (size_t)col0 * ngu;
+            // fused projection state of this group: per slot the atom being summed and its sums
+            int pcur[PROJ ? S : 1];
+            float2 pacc[PROJ ? S : 1][NP];
+            auto pflush = [&](int k) {
+                if (PROJ && pcur[k] >= 0) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        if (p < nvalid) red_add2(Cn + (size_t)(col0 + p) * A.natom + pcur[k], pacc[k][p]);
+                        pacc[k][p] = make_float2(0.f, 0.f);
+                    }
+                }
+            };
+            if (PROJ) {
+#pragma unroll
+                for (int k = 0; k < S; ++k) {
+                    pcur[k] = -1;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) pacc[k][p] = make_float2(0.f, 0.f);
+                }
+            }
             float4 q[NP][RY][QN];
             {   // planes z0 - R .. z0 + R - 1 of the queue; each stage then brings plane z + R
                 int wz = z0 - R < 0 ? z0 - R + n3 : z0 - R;
@@ -383,6 +417,10 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
                             float2 kb0[NP], kb1[NP];
 #pragma unroll
                             for (int p = 0; p < NP; ++p) kb0[p] = kb1[p] = make_float2(0.f, 0.f);
+                            // fused projection: weights of the two points in each slot's running sum, and the
+                            // slots whose second point belongs to another atom (added at once)
+                            float pw0[PROJ ? S : 1], pw1[PROJ ? S : 1];
+                            unsigned pstray = 0u;
                             if (KB) {
                                 const uint32_t Cg = st + kco;
 #pragma unroll
@@ -391,6 +429,18 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
                                     const float2 kv = lds64(st + L::OFF_KV + (uint32_t)(((k * TY + ty) * N1 + gx) * 4));
                                     const bool v0 = (unsigned)ka.x < (unsigned)A.natom;
                                     const bool v1 = (unsigned)ka.y < (unsigned)A.natom;
+                                    if (PROJ) {
+                                        const int a0 = (v0 && kv.x != 0.f) ? ka.x : -1;
+                                        const int a1 = (v1 && kv.y != 0.f) ? ka.y : -1;
+                                        const int t = a0 >= 0 ? a0 : a1;
+                                        if (t != pcur[k]) {
+                                            pflush(k);
+                                            pcur[k] = t;
+                                        }
+                                        pw0[k] = a0 >= 0 ? kv.x : 0.f;
+                                        pw1[k] = (a1 >= 0 && a1 == t) ? kv.y : 0.f;
+                                        if (a1 >= 0 && a1 != t) pstray |= 1u << k;
+                                    }
                                     const uint32_t c0p = Cg + (v0 ? (uint32_t)ka.x * 8u : 0u);
                                     const uint32_t c1p = Cg + (v1 ? (uint32_t)ka.y * 8u : 0u);
 #pragma unroll
@@ -460,6 +510,20 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
                                 if (p < nvalid)
                                     *reinterpret_cast<float4*>(Zg + p * ngu + g + rr * N1) =
                                         make_float4(o0.x, o0.y, o1.x, o1.y);
+                                if (PROJ) {
+#pragma unroll
+                                    for (int k = 0; k < S; ++k) {
+                                        pacc[k][p] = fma2(pw0[k], o0, pacc[k][p]);
+                                        pacc[k][p] = fma2(pw1[k], o1, pacc[k][p]);
+                                        if ((pstray >> k) & 1u) {   // rare: reread the slot of the second point
+                                            const int a1 = lds64i(st + L::OFF_KA + (uint32_t)(((k * TY + ty) * N1 + gx) * 4)).y;
+                                            const float w1 = lds64(st + L::OFF_KV + (uint32_t)(((k * TY + ty) * N1 + gx) * 4)).y;
+                                            if (p < nvalid)
+                                                red_add2(Cn + (size_t)(col0 + p) * A.natom + a1,
+                                                         make_float2(w1 * o1.x, w1 * o1.y));
+                                        }
+                                    }
+                                }
                             }
                         }
                         // this warp has read the stage: release it to the producer
@@ -468,6 +532,10 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
                         ++j;
                     }
                 }
+            }
+            if (PROJ && ok) {
+#pragma unroll
+                for (int k = 0; k < S; ++k) pflush(k);
             }
             f += z1 - z0;
         }
@@ -480,6 +548,15 @@ cheb_slab_kernel(const float2* __restrict__ Y, float2* __restrict__ Ynext, const
             const int s = j % D;
             if (!mb_wait(&full[s], (j / D) & 1)) break;
         }
+    }
+}
+
+// C[col][a] *= gamma_a over ne = ncol * natom coefficients (the fused projection's last factor)
+__global__ void kb_gamma_scale_kernel(float2* __restrict__ C, const double* __restrict__ gamma, int natom,
+                                      long long ne) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ne; i += (long long)gridDim.x * blockDim.x) {
+        const float g = (float)gamma[i % natom];
+        C[i] = make_float2(g * C[i].x, g * C[i].y);
     }
 }
 
@@ -584,8 +661,9 @@ void launch_slab_variant(sdft_ctx* c, int kpt, const float2* Y, const float2* Yp
     const int nblk = nper * nslab;
     const size_t dsm = slab_smem_bytes<N1, TY, NP, S, D>(c->natom);
     // the coefficient window of the last group reads at most (ncolE + NP - 1) * natom + 1 float2 of C
-    SDFT_REQUIRE(!haskb || (kbC == reinterpret_cast<const float2*>(c->C32) && ((uintptr_t)kbC & 15) == 0 &&
-                            (long long)(ncolE + NP - 1) * c->natom + 1 <= c->c32_elems),
+    SDFT_REQUIRE(!haskb || ((kbC == reinterpret_cast<const float2*>(c->C32) ||
+                             kbC == reinterpret_cast<const float2*>(c->C32b)) &&
+                            ((uintptr_t)kbC & 15) == 0 && (long long)(ncolE + NP - 1) * c->natom + 1 <= c->c32_elems),
                  SDFT_ERR_INVALID_ARG, "slab stencil: KB coefficient buffer misaligned or too short");
     SlabArgs A;
     for (int r = 0; r <= R; ++r) {
@@ -638,19 +716,44 @@ void launch_slab_variant(sdft_ctx* c, int kpt, const float2* Y, const float2* Yp
     int* err = stencil_error_flag(c);
     ScopedTimer timer(timed ? c : nullptr, SDFT_K_STENCIL,
                       (double)ncolE * (double)c->ng * sizeof(float2) * (prev ? 3.0 : 2.0));
-#define SDFT_SLAB(P, K)                                                                                          \
+#define SDFT_SLAB(P, K, J)                                                                                       \
     do {                                                                                                         \
-        auto kfn = cheb_slab_kernel<N1, TY, NP, RY, S, D, MINB, P, K>;                                            \
+        auto kfn = cheb_slab_kernel<N1, TY, NP, RY, S, D, MINB, P, K, J>;                                         \
         SDFT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));             \
-        kfn<<<grid, block, dsm, c->stream>>>(Y, Ynext, kbC, mfull, m6, mmid, mp, mv, mka, mkv, mq, A, err);          \
+        kfn<<<grid, block, dsm, c->stream>>>(Y, Ynext, kbC, Cn, mfull, m6, mmid, mp, mv, mka, mkv, mq, A, err);    \
     } while (0)
-    if (prev && haskb) SDFT_SLAB(true, true);
-    else if (!prev && haskb) SDFT_SLAB(false, true);
-    else if (prev && !haskb) SDFT_SLAB(true, false);
-    else SDFT_SLAB(false, false);
+    // fused projection of the output's KB coefficients into the buffer the caller offered
+    float2* Cn = (haskb && RY == 1) ? c->kb_next : nullptr;
+    if (Cn != nullptr) {
+        SDFT_REQUIRE(Cn != kbC && (Cn == reinterpret_cast<float2*>(c->C32) || Cn == reinterpret_cast<float2*>(c->C32b)),
+                     SDFT_ERR_INVALID_ARG, "slab stencil: fused projection target is not a KB coefficient buffer");
+        SDFT_CUDA(cudaMemsetAsync(Cn, 0, sizeof(float2) * (size_t)ncolE * c->natom, c->stream));
+    }
+    if constexpr (RY == 1) {
+        if (prev && Cn) SDFT_SLAB(true, true, true);
+        else if (!prev && Cn) SDFT_SLAB(false, true, true);
+        else if (prev && haskb) SDFT_SLAB(true, true, false);
+        else if (!prev && haskb) SDFT_SLAB(false, true, false);
+        else if (prev && !haskb) SDFT_SLAB(true, false, false);
+        else SDFT_SLAB(false, false, false);
+    } else {
+        if (prev && haskb) SDFT_SLAB(true, true, false);
+        else if (!prev && haskb) SDFT_SLAB(false, true, false);
+        else if (prev && !haskb) SDFT_SLAB(true, false, false);
+        else SDFT_SLAB(false, false, false);
+    }
 #undef SDFT_SLAB
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);
+    if (Cn != nullptr) {
+        // Cn[col][a] *= gamma_a
+        const long long ne = (long long)ncolE * c->natom;
+        kb_gamma_scale_kernel<<<(unsigned)std::min<long long>((ne + 255) / 256, 1024), 256, 0, c->stream>>>(
+            Cn, kb.gamma, c->natom, ne);
+        SDFT_CUDA(cudaGetLastError());
+        count_launch(c);
+        c->kb_next_done = true;
+    }
 }
 
 // instantiations used by the FP32 variant table (stencil_f32.cu)

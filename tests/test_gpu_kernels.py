@@ -167,6 +167,34 @@ def test_slab_stencil_variants_match_oracle(sd, variant, name, n, monkeypatch):
     assert _relerr(sd.unpack_block(y, sd.SDFT_MIXED, False), ref) < 3e-5 * 4
 
 
+# the step that also sums its output's KB coefficients (slab tiles with one row per thread) against
+# the separate projection pass, on the 64-atom cell (two KB slots per point, 64 projector spheres):
+# the same filter to FP32 rounding, and only the first step's projection is a separate launch
+@pytest.mark.parametrize("variant", [11, 12])
+def test_fused_kb_projection_matches_separate_pass(sd, variant, monkeypatch):
+    cell = workloads.lattice64_cell()
+    ns, m = cell.nstates, 8
+    monkeypatch.setenv("SDFT_STENCIL_VARIANT", str(variant))
+    X = workloads.initial_orbitals(3, cell.ngrid, ns)
+    V = np.random.default_rng(5).normal(-0.3, 0.2, cell.ngrid)
+    out, nproj = {}, {}
+    for fuse in ("1", "0"):
+        monkeypatch.setenv("SDFT_FUSE_KB", fuse)
+        ctx = _ctx(sd, cell, sd.SDFT_MIXED, ns)
+        sd.sdft_set_veff(ctx, 0, V)
+        x = sd.pack_block(X, sd.SDFT_MIXED)
+        y = torch.empty_like(x)
+        sd.sdft_set_timing(ctx, True)
+        sd.sdft_chebyshev_filter(ctx, 0, 0, sd.SDFT_MIXED, x, y, ns, m, 3.0, 90.0, -1.5)
+        torch.cuda.synchronize()
+        assert sd.sdft_get_stencil_variant(ctx, False)[0] == variant
+        nproj[fuse] = sd.sdft_get_kernel_stats(ctx)["kb_project"]["launches"]
+        out[fuse] = sd.unpack_block(y, sd.SDFT_MIXED, False)
+        sd.sdft_destroy(ctx)
+    assert nproj == {"1": 1, "0": m}
+    assert np.max(np.abs(out["1"] - out["0"])) < 2e-5 * np.max(np.abs(out["0"]))
+
+
 def test_slab_cell_has_at_most_two_kb_slots():
     # the slab test cells must stay within the tile's two staged KB slots per point
     for _, _, n in SLAB_VARIANTS:
