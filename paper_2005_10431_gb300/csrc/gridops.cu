@@ -353,31 +353,68 @@ __global__ void anderson_solve_kernel(const double* __restrict__ part, int nblk,
 template <int KIND>  // 0 FP64 real, 1 FP64 complex, 2 FP32 paired real, 3 FP32 complex
 __global__ void density_kernel(const void* __restrict__ X, const double* __restrict__ occ, int ncol, double scale,
                                long long ng, double* __restrict__ rho) {
+    // states past the last one with |occ| > 1e-14 change rho below FP64 rounding and are not read;
+    // the FP32 kinds square and weight in FP32 (the orbitals carry FP32 rounding already) and add
+    // groups of eight pairs into the FP64 sum, so that the few FP64 pipes of the GPU do not bound
+    // a pass that should stream the block at HBM speed
+    extern __shared__ float occf[];
+    __shared__ int nlast;
+    if (threadIdx.x == 0) nlast = 0;
+    __syncthreads();
+    for (int n = threadIdx.x; n < ncol; n += blockDim.x) {
+        const double o = occ[n];
+        if (KIND >= 2) occf[n] = (float)o;
+        if (fabs(o) > 1e-14) atomicMax(&nlast, n + 1);
+    }
+    __syncthreads();
+    const int nc = nlast;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
         double s = 0.0;
         if (KIND == 0) {
             const double* x = (const double*)X;
-            for (int n = 0; n < ncol; ++n) {
+            for (int n = 0; n < nc; ++n) {
                 const double v = x[(long long)n * ng + g];
                 s += occ[n] * v * v;
             }
         } else if (KIND == 1) {
             const double2* x = (const double2*)X;
-            for (int n = 0; n < ncol; ++n) {
+            for (int n = 0; n < nc; ++n) {
                 const double2 v = x[(long long)n * ng + g];
                 s += occ[n] * (v.x * v.x + v.y * v.y);
             }
         } else if (KIND == 2) {
             const float2* x = (const float2*)X;
-            for (int p = 0; p < ncol / 2; ++p) {
-                const float2 v = x[(long long)p * ng + g];
-                s += occ[2 * p] * (double)v.x * v.x + occ[2 * p + 1] * (double)v.y * v.y;
+            const int np = (nc + 1) / 2;
+            for (int p0 = 0; p0 < np; p0 += 8) {
+                float sf = 0.f;
+                if (p0 + 8 <= np) {   // eight loads in flight
+                    float2 v[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[i] = x[(long long)(p0 + i) * ng + g];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        sf = fmaf(occf[2 * (p0 + i)], v[i].x * v[i].x, sf);
+                        sf = fmaf(occf[2 * (p0 + i) + 1], v[i].y * v[i].y, sf);
+                    }
+                } else {
+                    for (int p = p0; p < np; ++p) {
+                        const float2 v = x[(long long)p * ng + g];
+                        sf = fmaf(occf[2 * p], v.x * v.x, sf);
+                        sf = fmaf(occf[2 * p + 1], v.y * v.y, sf);
+                    }
+                }
+                s += (double)sf;
             }
         } else {
             const float2* x = (const float2*)X;
-            for (int n = 0; n < ncol; ++n) {
-                const float2 v = x[(long long)n * ng + g];
-                s += occ[n] * ((double)v.x * v.x + (double)v.y * v.y);
+            for (int n0 = 0; n0 < nc; n0 += 8) {
+                float sf = 0.f;
+                const int n1 = min(nc, n0 + 8);
+                for (int n = n0; n < n1; ++n) {
+                    const float2 v = x[(long long)n * ng + g];
+                    sf = fmaf(occf[n], v.x * v.x + v.y * v.y, sf);
+                }
+                s += (double)sf;
             }
         }
         rho[g] += scale * s;
@@ -1702,12 +1739,14 @@ void density_accumulate(sdft_ctx* c, int precision, bool cplx, const void* X, co
     const double scale = weight / c->dV;
     const unsigned nb = nblocks(c->ng);
     ScopedTimer timer(c, SDFT_K_DENSITY, (double)block_elems_bytes(c, precision, cplx, ncol));
+    const size_t sm32 = sizeof(float) * (size_t)ncol;   // FP32 copy of the occupations
+    SDFT_REQUIRE(sm32 <= 48 * 1024, SDFT_ERR_INVALID_ARG, "density: too many states for one block's occupations");
     if (precision == SDFT_FP64) {
         if (cplx) density_kernel<1><<<nb, 256, 0, c->stream>>>(X, occ, ncol, scale, c->ng, rho);
         else density_kernel<0><<<nb, 256, 0, c->stream>>>(X, occ, ncol, scale, c->ng, rho);
     } else {
-        if (cplx) density_kernel<3><<<nb, 256, 0, c->stream>>>(X, occ, ncol, scale, c->ng, rho);
-        else density_kernel<2><<<nb, 256, 0, c->stream>>>(X, occ, ncol, scale, c->ng, rho);
+        if (cplx) density_kernel<3><<<nb, 256, sm32, c->stream>>>(X, occ, ncol, scale, c->ng, rho);
+        else density_kernel<2><<<nb, 256, sm32, c->stream>>>(X, occ, ncol, scale, c->ng, rho);
     }
     SDFT_CUDA(cudaGetLastError());
     count_launch(c);
