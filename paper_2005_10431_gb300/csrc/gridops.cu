@@ -1311,10 +1311,10 @@ static int aar_fp32_mg(sdft_ctx* c, const float* b, float* x, double tol_rel, in
     const long long n = c->ng;
     const float omega = 0.7f, beta = 0.7f;
     const int m = 5, p = 3;
-    // reduction grids: the history Gram's partials (m (m + 1) / 2 + m + 1 = 21 per block) fill at most
-    // 296 * 21 of the 12 288 doubles from scal + 4096; the single dot's fill 512 of the 1 024 from
-    // scal + 2048 (two blocks per SM: these are L2-resident vectors, latency-bound with fewer blocks)
-    constexpr int NB_G = 296, NB_R = 512;
+    // reduction grids: the history Gram's partials (m (m + 1) / 2 + m + 1 = 21 per block) fill 64 * 21
+    // of the 12 288 doubles from scal + 4096, the single dot's 64 of the 1 024 from scal + 2048 (more
+    // blocks did not shorten the Gram, and the one-CTA solve then sums more partials)
+    constexpr int NB_G = 64, NB_R = 64;
     float* r = c->work32 + 1 * n;
     float* xprev = c->work32 + 2 * n;
     float* fprev = c->work32 + 3 * n;
