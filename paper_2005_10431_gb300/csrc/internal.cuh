@@ -155,7 +155,7 @@ struct sdft_ctx {
     cusolverDnHandle_t solver = nullptr;
     syevjInfo_t syevj_params = nullptr;
     int eig_method = -1;          // -1: batched Jacobi for n <= 64, FP32 + FP64 refinement for real mixed-precision
-                                  //     n <= 160, else sygvd/hegvd; 0: sygvd/hegvd; 1: sygvj (real);
+                                  //     n <= 1024, else sygvd/hegvd; 0: sygvd/hegvd; 1: sygvj (real);
                                   //  2: FP32 + refinement wherever it applies, without fallback
     double* reig_buf = nullptr;   // scratch of the refined eigensolver (allocated on first use)
     int reig_nmax = 0;            // the largest n that scratch holds
