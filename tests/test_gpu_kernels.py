@@ -195,6 +195,30 @@ def test_fused_kb_projection_matches_separate_pass(sd, variant, monkeypatch):
     assert np.max(np.abs(out["1"] - out["0"])) < 2e-5 * np.max(np.abs(out["0"]))
 
 
+def test_full_size_block_matches_oracle_on_sampled_orbitals(sd):
+    # the 64-atom cell at full size -- 80^3 points, 154 states + 26 buffer states, the block the
+    # benchmark filters, with the stencil tile the autotuner picks for it as in the benchmark: a
+    # degree-20 Chebyshev filter and H X of the whole block on the GPU against the oracle applied
+    # to three sampled orbitals (the columns are independent), at every grid point
+    cell = workloads.lattice64_cell()
+    ns = cell.nstates + 26
+    ctx = sd.sdft_create(cell.L, cell.n, cell.pos, cell.types, cell.species,
+                         dict(nstates=cell.nstates, nbuffer=26, precision=sd.SDFT_MIXED))
+    V = np.random.default_rng(5).normal(-0.3, 0.2, cell.ngrid)
+    sd.sdft_set_veff(ctx, 0, V)
+    X = workloads.initial_orbitals(7, cell.ngrid, ns)
+    x = sd.pack_block(X, sd.SDFT_MIXED)
+    y = torch.empty_like(x)
+    P, E = model.projectors(cell), model.kb_energies(cell)
+    cols = [0, 77, ns - 1]
+    sd.sdft_chebyshev_filter(ctx, 0, 0, sd.SDFT_MIXED, x, y, ns, 20, 1.0, 250.0, -1.5)
+    ref = chefsi.chebyshev_filter(lambda Z: ham.apply_h(cell, Z, V, P, E), X[cols], 20, 1.0, 250.0, -1.5)
+    assert _relerr(sd.unpack_block(y, sd.SDFT_MIXED, False)[cols], ref) < 3e-5 * 20
+    sd.sdft_apply_h(ctx, 0, 0, sd.SDFT_MIXED, x, y, ns)
+    assert _relerr(sd.unpack_block(y, sd.SDFT_MIXED, False)[cols], ham.apply_h(cell, X[cols], V, P, E)) < 2e-5
+    sd.sdft_destroy(ctx)
+
+
 def test_slab_cell_has_at_most_two_kb_slots():
     # the slab test cells must stay within the tile's two staged KB slots per point
     for _, _, n in SLAB_VARIANTS:
