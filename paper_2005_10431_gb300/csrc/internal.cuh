@@ -232,7 +232,7 @@ struct sdft_ctx {
     float2* kb_next = nullptr;    // set around one FP32 step launch: where a slab step may also write the KB
     bool kb_next_done = false;    //   coefficients of its output (kb_next_done: it did)
     bool fuse_kb_projection = true;   // SDFT_FUSE_KB=0: always the separate projection pass
-    bool stencil_fuse = true;         // the autotuner's verdict: fused projection (where offered) faster
+    bool stencil_fuse = true;         // the autotuner's finding: fused projection (where offered) faster
     double* C64 = nullptr;
 
     // mixing history
