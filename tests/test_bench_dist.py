@@ -57,3 +57,20 @@ def test_reference_arm_under_torchrun_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["value"] > 0
+
+
+def test_probe_grids_and_pipe_flop_count():
+    # host logic of the probe modes: --grid G or n1,n2,n3 keeps the cell and replaces the grid;
+    # the tensor-pipe flop count of the BF16x3 GEMMs as the kernels tile them (three split
+    # products; 128-row tiles; Gram column tiles rounded up to 16 and stacked [Y; HY], upper
+    # triangle only; rotation blocks of at most 256 columns)
+    import bench
+    c = bench.cell_for("lattice216_120", "120,40,40")
+    assert c.n == (120, 40, 40) and c.natom == 216
+    assert bench.cell_for("lattice64_80", "40").n == (40, 40, 40)
+    ng, ns = 4096, 128
+    gram, rot = bench.gemm_pipe_flops(ng, ns)
+    assert gram == 3 * 2 * 128 * (2 * 128) * ng      # one tile pair, N = 2 * 128
+    assert rot == 3 * 2 * ng * 128 * 128             # one block of 128 (rounded to 16) columns, K = 128
+    gram2, _ = bench.gemm_pipe_flops(ng, 130)       # two tiles: widths 128 and 16 (2 rounded up)
+    assert gram2 == 3 * 2 * 128 * (2 * 128 + 2 * 16 + 2 * 16) * ng
